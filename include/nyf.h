@@ -1,0 +1,192 @@
+/*
+ * nyf.h -- C ABI of libnyf, the GB300 (sm_103a) Nystrom kernel filter.
+ *
+ * Method: P. Nair and K. N. Chaudhury, "Fast High-Dimensional Kernel
+ * Filtering", arXiv 1901.06112.  The exact filter is Eq. (1); the fast filter
+ * is Algorithm 1, i.e. Eqs. (9)-(12) for the Nystrom factors and
+ * Eqs. (14)-(15) for the output, with k-means landmarks (Sec. III).
+ *
+ * Conventions shared by every entry point
+ *  - Images are HWC float32, row-major, contiguous: element (y, x, c) of an
+ *    H x W x C image is at index (y * W + x) * C + c.  A "guide" is an
+ *    H x W x rho image (the paper's p : Omega -> R^rho).
+ *  - All data pointers are DEVICE pointers owned by the caller unless stated
+ *    otherwise.  The library never allocates device memory: scratch space is
+ *    the caller's workspace `ws` of at least nyf_workspace_size() bytes,
+ *    256-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call only enqueues work on it; none synchronises, except
+ *    nyf_get_stats.
+ *  - Argument errors are detected on the host before anything is enqueued and
+ *    returned at once.  Errors found on the device while the work runs (no
+ *    eigenvalue kept, a draw that did not finish) are latched into a sticky
+ *    status word inside `ws` and read back with nyf_get_stats.
+ *  - Range kernel kappa(t, s) = exp(-||t - s||^2 / (2 sigma_r^2)) (sigma_r is
+ *    the paper's theta, Sec. IV setup).  Spatial kernel omega(z) =
+ *    exp(-||z||^2 / (2 sigma_s^2)) on the window ||z||_inf <= S (S defaults to
+ *    ceil(3 sigma_s), Sec. IV setup) or a box of ones; the window is clipped
+ *    to the image (zero padding).
+ *  - Eq. (12) divides by the eigenvalues alpha_k of A; only modes with
+ *    alpha_k > eig_rel_tol * alpha_max are used (their number is the rank r).
+ */
+#ifndef NYF_H
+#define NYF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NYF_MAX_K 64        /* largest number of landmarks m0 */
+#define NYF_MAX_RHO 160     /* largest guide dimension rho */
+#define NYF_MAX_S 32        /* largest window radius S */
+#define NYF_MAX_CHANNELS 64 /* largest number of image channels n */
+
+typedef enum {
+  NYF_OK = 0,
+  NYF_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
+  NYF_ERR_UNSUPPORTED = 2, /* valid but outside what this build implements */
+  NYF_ERR_WORKSPACE = 3,   /* ws is NULL, misaligned or smaller than required */
+  NYF_ERR_NUMERIC = 4,     /* device: no eigenvalue kept (rank 0) or non-finite data */
+  NYF_ERR_CUDA = 5,        /* a CUDA launch or copy failed */
+  NYF_ERR_TIMEOUT = 6      /* device: a bounded loop reached its limit */
+} nyf_status;
+
+typedef enum { NYF_FP32 = 0, NYF_BF16 = 1 } nyf_precision;
+typedef enum { NYF_GAUSSIAN = 0, NYF_BOX = 1 } nyf_spatial;
+
+/* Filter parameters (Sec. IV setup; Algorithm 1's m0 is K). */
+typedef struct {
+  float sigma_s;      /* spatial Gaussian std; unused for NYF_BOX unless S <= 0 */
+  float sigma_r;      /* range Gaussian std (theta), > 0 */
+  int K;              /* number of landmarks m0, 1..NYF_MAX_K */
+  int kmeans_iters;   /* Lloyd iterations, >= 0 (0: landmarks = the drawn pixels) */
+  uint64_t seed;      /* SplitMix64 seed of the initial-landmark and subsample draws */
+  double eig_rel_tol; /* tau: modes with alpha_k > tau * alpha_max are kept, >= 0 */
+  int precision;      /* nyf_precision: storage/arithmetic of the per-pixel features */
+  int spatial;        /* nyf_spatial */
+  int S;              /* window radius; <= 0 means ceil(3 sigma_s) */
+  int patch_radius;   /* NLM: guide = (2r+1)^2 x n patch, reflect-101 border */
+  float sample_frac;  /* fraction of pixels k-means clusters, (0, 1] */
+} nyf_params;
+
+/* Device-side results of the last call on a workspace (nyf_get_stats). */
+typedef struct {
+  int status;              /* sticky nyf_status of the work run on this workspace */
+  int rank;                /* kept modes r */
+  double qerr;             /* k-means quantisation error e for the final landmarks (Sec. III) */
+  double alpha_max;        /* largest eigenvalue of A */
+  double alpha_min_kept;   /* smallest kept eigenvalue */
+  long long eta_small;     /* pixels with eta_hat <= 1e-6 * sum(omega) (Eq. (15)) */
+  float grad_sigma_r;      /* last backward: dL/d sigma_r */
+  float grad_sigma_s;      /* last backward: dL/d sigma_s */
+} nyf_stats;
+
+/* Bytes of workspace that the filter calls need for an H x W image with n
+ * channels and guide dimension rho (rho is ignored for NLM, whose guide
+ * dimension is n (2r+1)^2).  The same workspace serves nyf_kmeans and
+ * nyf_features on N = H * W rows.  Returns 0 if the arguments are invalid. */
+size_t nyf_workspace_size(int H, int W, int n, int rho, const nyf_params* params);
+
+/* k-means landmark selection (Sec. III "we partition R into m0 disjoint sets
+ * using k-means"; Algorithm 1, clustering step).
+ *   X         N x rho rows to cluster (device, read only)
+ *   init_idx  K distinct row indices of the initial centroids (device int64),
+ *             or NULL: drawn on the device as the first K distinct values of
+ *             SplitMix64(seed) output mod N
+ *   centroids K x rho output (device)
+ *   labels    N int32 output for the final centroids, or NULL
+ *   qerr      1 double output: quantisation error e for the final centroids, or NULL
+ * Each iteration assigns every row to its nearest centroid (ties to the
+ * lowest index) and moves each centroid to the mean of its members (an empty
+ * cluster keeps its centroid).  Reductions run in a fixed order, so results
+ * are bitwise reproducible. */
+nyf_status nyf_kmeans(const float* X, int64_t N, int rho, int K, int iters, uint64_t seed,
+                      const int64_t* init_idx, float* centroids, int32_t* labels, double* qerr,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* Nystrom per-pixel features (Eqs. (9)-(12)).  For landmarks mu (K x rho):
+ * A(i,j) = kappa(mu_i, mu_j) is decomposed in FP64 (Eq. (10)), and for every
+ * row p_x of `guide` (N x rho) and kept mode k
+ *     phi_k(x) = sum_m kappa(p_x, mu_m) w_mk / sqrt(alpha_k)
+ * = sqrt(alpha_k) v_k(x) of Eq. (12), so that K-hat = sum_k phi_k phi_k^T.
+ *   phi     output, K planes of N values (plane k at phi + k * N), float32
+ *           (NYF_FP32) or bfloat16 (NYF_BF16); planes k >= r are left unchanged
+ *   rank    1 int output (device) or NULL
+ *   alphas  K doubles output (device): all eigenvalues of A, descending, or NULL
+ * Eigenvector signs are not fixed by Eq. (10); phi is unique up to the sign
+ * of each plane (and rotations within equal eigenvalues). */
+nyf_status nyf_features(const float* guide, int64_t N, int rho, const float* landmarks, int K,
+                        float sigma_r, double eig_rel_tol, int precision, void* phi, int* rank,
+                        double* alphas, void* ws, size_t ws_bytes, void* stream);
+
+/* Nystrom bilateral filter, Algorithm 1 with output Eqs. (14)-(15).
+ *   f          H x W x n image (device)
+ *   guide      H x W x rho guide (joint BLF), or NULL: guide = f (rho must equal n)
+ *   landmarks  K x rho landmarks (device), or NULL: k-means on every pixel
+ *              of the guide (params->kmeans_iters, params->seed)
+ *   out        H x W x n output g_hat = zeta / eta (device); pixels where
+ *              eta_hat <= 0 are not clamped (Eq. (15) can vanish)
+ * The workspace keeps the landmarks, factors, features and eta for
+ * nyf_filter_blf_backward. */
+nyf_status nyf_filter_blf(const float* f, const float* guide, int H, int W, int n, int rho,
+                          const nyf_params* params, const float* landmarks, float* out,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* Nystrom nonlocal means: guide p(x) = the (2r+1) x (2r+1) x n patch around x
+ * (Sec. II; Sec. IV "Color NLM", rho = n (2r+1)^2), reflect-101 border,
+ * components ordered (dy, dx, c); box window of radius params->S.
+ * k-means runs on round(sample_frac * N) pixels, one drawn per stratum of the
+ * row-major pixel order with SplitMix64(seed ^ 0xA5A5A5A5A5A5A5A5).
+ *   landmarks  K x rho patch landmarks (device) or NULL (k-means). */
+nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params* params,
+                          const float* landmarks, float* out, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/* Adjoint of nyf_filter_blf (the paper has no gradients; derived from
+ * Eqs. (9)-(15)).  Must follow the nyf_filter_blf call that produced `out`
+ * on the same workspace, with the same f, guide and params.  Landmarks are
+ * held fixed; the window radius S is held at its forward value; the kept
+ * modes are held fixed.  Given grad_out = dL/d g_hat (H x W x n):
+ *   grad_f      H x W x n output dL/df; if guide was NULL this is the total
+ *               derivative (image and guide are the same tensor)
+ *   grad_guide  H x W x rho output dL/dp for a joint guide, or NULL
+ *   grad_sigma  2 floats output (device): dL/d sigma_r, dL/d sigma_s
+ *               (dL/d sigma_s is 0 for the box window). */
+nyf_status nyf_filter_blf_backward(const float* f, const float* guide, int H, int W, int n,
+                                   int rho, const nyf_params* params, const float* out,
+                                   const float* grad_out, float* grad_f, float* grad_guide,
+                                   float* grad_sigma, void* ws, size_t ws_bytes, void* stream);
+
+/* Copies the device-side results of the last call on `ws` to *out.  This is
+ * the one call that synchronises `stream`. */
+nyf_status nyf_get_stats(const void* ws, nyf_stats* out, void* stream);
+
+/* Per-stage timing (instrumentation for measurement, off by default).  While
+ * enabled, each filter call records CUDA events on its stream around its
+ * stages: 0 landmarks (subsample + k-means), 1 eigendecomposition,
+ * 2 features, 3 convolution + combine, 4 backward convolutions,
+ * 5 backward features, 6 backward landmark-kernel term.  nyf_get_timing
+ * synchronises on the events of the last instrumented call and writes the
+ * elapsed milliseconds of up to `max_stages` stages (-1 for a stage that did
+ * not run); it returns the number of stages written.  Not for use while a
+ * stream is being captured into a CUDA graph. */
+void nyf_set_timing(int enable);
+int nyf_get_timing(float* ms, int max_stages);
+
+/* Number of kernels this process has launched through libnyf so far. */
+long long nyf_launch_count(void);
+
+/* Static description of a status code. */
+const char* nyf_status_string(nyf_status s);
+
+/* ABI version (major * 100 + minor). */
+int nyf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NYF_H */

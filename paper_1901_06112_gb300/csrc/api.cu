@@ -1,0 +1,406 @@
+// The C ABI of libnyf (include/nyf.h): argument checks, workspace layout and
+// the order of the stages of Algorithm 1.  Everything is enqueued on the
+// caller's stream; nothing here allocates device memory or synchronises
+// (except nyf_get_stats).
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "nyf_internal.cuh"
+
+namespace nyf {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+WsLayout ws_layout(const WsShape& s) {
+  WsLayout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  const size_t K = (size_t)s.K, rho = (size_t)s.rho, N = (size_t)s.N, Ns = (size_t)s.Ns;
+  L.state = take(sizeof(DevState));
+  L.landmarks = take(sizeof(float) * K * rho);
+  L.what = take(sizeof(float) * K * K);
+  L.init_idx = take(sizeof(int64_t) * K);
+  L.km_part = take(sizeof(float) * (size_t)kKmeansBlocks * K * (rho + 1));
+  L.km_qpart = take(sizeof(float) * (size_t)kKmeansBlocks);
+  const bool gather = s.gather || Ns < N;
+  L.sample_idx = take(sizeof(int64_t) * (gather ? Ns : 0));
+  L.sample_x = take(sizeof(float) * (gather ? Ns * rho : 0));
+  L.phi = take((s.bf16 ? 2 : 4) * K * N);
+  L.eta = take(sizeof(float) * N);
+  L.zeta = take(sizeof(float) * N * (size_t)s.n);
+  L.dphi = take(sizeof(float) * K * N);
+  L.gpart = take(sizeof(float) * (size_t)kKmeansBlocks * (K * K + K * rho + 8));
+  L.total = o;
+  return L;
+}
+
+}  // namespace nyf
+
+using namespace nyf;
+
+namespace {
+
+// ---- per-stage CUDA-event timing (instrumentation only)
+constexpr int kStages = 7;
+std::atomic<int> g_timing{0};
+std::mutex g_timing_mu;
+bool g_events_ready = false;
+cudaEvent_t g_ev[kStages][2];
+int g_ran[kStages];
+
+struct Stage {
+  cudaStream_t st;
+  int id;
+  bool on;
+  Stage(cudaStream_t s, int i) : st(s), id(i), on(g_timing.load() != 0 && g_events_ready) {
+    if (on) cudaEventRecord(g_ev[id][0], st);
+  }
+  ~Stage() {
+    if (on) {
+      cudaEventRecord(g_ev[id][1], st);
+      g_ran[id] = 1;
+    }
+  }
+};
+
+void timing_begin(int first, int last) {
+  if (!g_timing.load() || !g_events_ready) return;
+  for (int i = first; i <= last; ++i) g_ran[i] = 0;
+}
+
+int window_radius(const nyf_params* p) {
+  if (p->S > 0) return p->S;
+  return (int)ceil(3.0 * (double)p->sigma_s);
+}
+
+int64_t subsample_rows(int64_t N, float frac) {
+  int64_t v = (int64_t)floor((double)frac * (double)N + 0.5);
+  if (v < 1) v = 1;
+  if (v > N) v = N;
+  return v;
+}
+
+nyf_status check_params(const nyf_params* p, int n) {
+  if (!p) return NYF_ERR_INVALID_ARG;
+  if (!(p->sigma_r > 0.f) || !isfinite(p->sigma_r)) return NYF_ERR_INVALID_ARG;
+  if (p->K < 1 || p->K > NYF_MAX_K) return NYF_ERR_INVALID_ARG;
+  if (p->kmeans_iters < 0) return NYF_ERR_INVALID_ARG;
+  if (!(p->eig_rel_tol >= 0.0) || !isfinite(p->eig_rel_tol)) return NYF_ERR_INVALID_ARG;
+  if (p->precision != NYF_FP32 && p->precision != NYF_BF16) return NYF_ERR_INVALID_ARG;
+  if (p->spatial != NYF_GAUSSIAN && p->spatial != NYF_BOX) return NYF_ERR_INVALID_ARG;
+  if (p->spatial == NYF_GAUSSIAN && (!(p->sigma_s > 0.f) || !isfinite(p->sigma_s)))
+    return NYF_ERR_INVALID_ARG;
+  if (p->spatial == NYF_BOX && p->S <= 0 && (!(p->sigma_s > 0.f) || !isfinite(p->sigma_s)))
+    return NYF_ERR_INVALID_ARG;
+  if (!(p->sample_frac > 0.f) || p->sample_frac > 1.f) return NYF_ERR_INVALID_ARG;
+  if (n < 1 || n > NYF_MAX_CHANNELS) return NYF_ERR_INVALID_ARG;
+  const int S = window_radius(p);
+  if (S < 1) return NYF_ERR_INVALID_ARG;
+  if (S > NYF_MAX_S) return NYF_ERR_UNSUPPORTED;
+  if (p->patch_radius < 0) return NYF_ERR_INVALID_ARG;
+  return NYF_OK;
+}
+
+bool ws_ok(const void* ws, size_t have, size_t need) {
+  return ws && (reinterpret_cast<uintptr_t>(ws) & 255) == 0 && have >= need;
+}
+
+nyf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? NYF_OK : NYF_ERR_CUDA; }
+
+#define NYF_TRY(expr)                                   \
+  do {                                                  \
+    cudaError_t _e = (expr);                            \
+    if (_e != cudaSuccess) return NYF_ERR_CUDA;         \
+  } while (0)
+
+bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3) == 0; }
+
+int nlm_rho(int n, int r) { return (2 * r + 1) * (2 * r + 1) * n; }
+
+// Shared argument checks of the filter entry points.
+nyf_status check_filter(const float* f, int H, int W, int n, int rho, const nyf_params* p,
+                        const float* out) {
+  nyf_status s = check_params(p, n);
+  if (s != NYF_OK) return s;
+  if (!f || !out || !aligned4(f) || !aligned4(out)) return NYF_ERR_INVALID_ARG;
+  if (H < 1 || W < 1 || (int64_t)H * W > ((int64_t)1 << 31)) return NYF_ERR_INVALID_ARG;
+  if (rho < 1 || rho > NYF_MAX_RHO) return NYF_ERR_INVALID_ARG;
+  if (kmeans_smem_bytes(p->K, rho) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
+  return NYF_OK;
+}
+
+WsShape shape_for(int H, int W, int n, int rho, const nyf_params* p) {
+  WsShape s;
+  s.N = (int64_t)H * W;
+  s.n = n;
+  s.rho = rho;
+  s.K = p->K;
+  s.Ns = subsample_rows(s.N, p->sample_frac);
+  s.bf16 = p->precision == NYF_BF16;
+  s.gather = p->patch_radius > 0;
+  return s;
+}
+
+// Landmarks into ws: copied, or k-means on the rows X (N x rho).
+nyf_status stage_landmarks(const float* X_full, int64_t N, int rho, const nyf_params* p,
+                           const float* landmarks, char* w, const WsLayout& L, bool nlm,
+                           const float* f, int H, int W, int n, cudaStream_t st) {
+  DevState* state = reinterpret_cast<DevState*>(w + L.state);
+  float* lm = reinterpret_cast<float*>(w + L.landmarks);
+  if (landmarks) {
+    NYF_TRY(cudaMemcpyAsync(lm, landmarks, sizeof(float) * p->K * rho, cudaMemcpyDeviceToDevice, st));
+    return NYF_OK;
+  }
+  const int64_t Ns = subsample_rows(N, p->sample_frac);
+  if (p->K > Ns) return NYF_ERR_INVALID_ARG;
+  const float* X = X_full;
+  if (nlm) {
+    NYF_TRY(launch_nlm_sample(f, H, W, n, p->patch_radius, Ns, p->seed,
+                              reinterpret_cast<int64_t*>(w + L.sample_idx),
+                              reinterpret_cast<float*>(w + L.sample_x), st));
+    X = reinterpret_cast<const float*>(w + L.sample_x);
+  } else if (Ns < N) {
+    NYF_TRY(launch_sample_rows(X_full, N, rho, Ns, p->seed,
+                               reinterpret_cast<int64_t*>(w + L.sample_idx),
+                               reinterpret_cast<float*>(w + L.sample_x), st));
+    X = reinterpret_cast<const float*>(w + L.sample_x);
+  }
+  NYF_TRY(launch_draw_init(X, Ns, rho, p->K, p->seed, nullptr,
+                           reinterpret_cast<int64_t*>(w + L.init_idx), lm, state, st));
+  NYF_TRY(launch_kmeans(X, Ns, rho, p->K, p->kmeans_iters, lm, nullptr, nullptr,
+                        reinterpret_cast<float*>(w + L.km_part),
+                        reinterpret_cast<float*>(w + L.km_qpart), state, st));
+  return NYF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nyf_version(void) { return 100; }
+
+void nyf_set_timing(int enable) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  if (enable && !g_events_ready) {
+    for (int i = 0; i < kStages; ++i) {
+      cudaEventCreate(&g_ev[i][0]);
+      cudaEventCreate(&g_ev[i][1]);
+      g_ran[i] = 0;
+    }
+    g_events_ready = true;
+  }
+  g_timing.store(enable ? 1 : 0);
+}
+
+int nyf_get_timing(float* ms, int max_stages) {
+  if (!ms || max_stages < 1) return 0;
+  const int n = max_stages < kStages ? max_stages : kStages;
+  for (int i = 0; i < n; ++i) {
+    ms[i] = -1.f;
+    if (g_events_ready && g_ran[i]) {
+      float t = -1.f;
+      if (cudaEventSynchronize(g_ev[i][1]) == cudaSuccess &&
+          cudaEventElapsedTime(&t, g_ev[i][0], g_ev[i][1]) == cudaSuccess)
+        ms[i] = t;
+    }
+  }
+  return n;
+}
+
+long long nyf_launch_count(void) { return g_launches.load(); }
+
+const char* nyf_status_string(nyf_status s) {
+  switch (s) {
+    case NYF_OK: return "ok";
+    case NYF_ERR_INVALID_ARG: return "invalid argument";
+    case NYF_ERR_UNSUPPORTED: return "unsupported configuration";
+    case NYF_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case NYF_ERR_NUMERIC: return "numeric failure (no eigenvalue kept or non-finite data)";
+    case NYF_ERR_CUDA: return "CUDA launch or copy failed";
+    case NYF_ERR_TIMEOUT: return "bounded device loop reached its limit";
+  }
+  return "unknown status";
+}
+
+size_t nyf_workspace_size(int H, int W, int n, int rho, const nyf_params* p) {
+  if (!p || H < 1 || W < 1 || n < 1 || p->K < 1 || p->K > NYF_MAX_K) return 0;
+  if (p->patch_radius > 0) rho = nlm_rho(n, p->patch_radius);
+  if (rho < 1 || rho > NYF_MAX_RHO) return 0;
+  if (!(p->sample_frac > 0.f) || p->sample_frac > 1.f) return 0;
+  return ws_layout(shape_for(H, W, n, rho, p)).total;
+}
+
+nyf_status nyf_kmeans(const float* X, int64_t N, int rho, int K, int iters, uint64_t seed,
+                      const int64_t* init_idx, float* centroids, int32_t* labels, double* qerr,
+                      void* ws, size_t ws_bytes, void* stream) {
+  if (!X || !centroids || N < 1 || N > ((int64_t)1 << 31) || rho < 1 || rho > NYF_MAX_RHO ||
+      K < 1 || K > NYF_MAX_K || K > N || iters < 0)
+    return NYF_ERR_INVALID_ARG;
+  if (kmeans_smem_bytes(K, rho) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
+  WsShape s{N, 1, rho, K, N, false, false};
+  const WsLayout L = ws_layout(s);
+  if (!ws_ok(ws, ws_bytes, L.km_qpart + sizeof(float) * kKmeansBlocks)) return NYF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  DevState* state = reinterpret_cast<DevState*>(w + L.state);
+  NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
+  NYF_TRY(launch_draw_init(X, N, rho, K, seed, init_idx, reinterpret_cast<int64_t*>(w + L.init_idx),
+                           centroids, state, st));
+  NYF_TRY(launch_kmeans(X, N, rho, K, iters, centroids, labels, qerr,
+                        reinterpret_cast<float*>(w + L.km_part),
+                        reinterpret_cast<float*>(w + L.km_qpart), state, st));
+  return NYF_OK;
+}
+
+nyf_status nyf_features(const float* guide, int64_t N, int rho, const float* landmarks, int K,
+                        float sigma_r, double eig_rel_tol, int precision, void* phi, int* rank,
+                        double* alphas, void* ws, size_t ws_bytes, void* stream) {
+  if (!guide || !landmarks || !phi || N < 1 || N > ((int64_t)1 << 31) || rho < 1 ||
+      rho > NYF_MAX_RHO || K < 1 || K > NYF_MAX_K || !(sigma_r > 0.f) || !isfinite(sigma_r) ||
+      !(eig_rel_tol >= 0.0) || (precision != NYF_FP32 && precision != NYF_BF16))
+    return NYF_ERR_INVALID_ARG;
+  if (sizeof(float) * ((size_t)K * rho + (size_t)K * K) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
+  WsShape s{N, 1, rho, K, N, precision == NYF_BF16, false};
+  const WsLayout L = ws_layout(s);
+  if (!ws_ok(ws, ws_bytes, L.what + sizeof(float) * K * K)) return NYF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  DevState* state = reinterpret_cast<DevState*>(w + L.state);
+  float* what = reinterpret_cast<float*>(w + L.what);
+  NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
+  NYF_TRY(launch_eig(landmarks, K, rho, sigma_r, eig_rel_tol, what, alphas, rank, state, st));
+  NYF_TRY(launch_features(guide, N, rho, landmarks, K, sigma_r, what, state, phi,
+                          precision == NYF_BF16, st));
+  return NYF_OK;
+}
+
+nyf_status nyf_filter_blf(const float* f, const float* guide, int H, int W, int n, int rho,
+                          const nyf_params* p, const float* landmarks, float* out, void* ws,
+                          size_t ws_bytes, void* stream) {
+  if (!p || p->patch_radius != 0) return NYF_ERR_INVALID_ARG;
+  if (!guide) {
+    if (rho != n) return NYF_ERR_INVALID_ARG;
+    guide = f;
+  }
+  nyf_status s = check_filter(f, H, W, n, rho, p, out);
+  if (s != NYF_OK) return s;
+  if (!aligned4(guide)) return NYF_ERR_INVALID_ARG;
+  const WsLayout L = ws_layout(shape_for(H, W, n, rho, p));
+  if (!ws_ok(ws, ws_bytes, L.total)) return NYF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  DevState* state = reinterpret_cast<DevState*>(w + L.state);
+  const int64_t N = (int64_t)H * W;
+  const bool bf16 = p->precision == NYF_BF16;
+  NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
+  timing_begin(0, 3);
+  {
+    Stage t(st, 0);
+    s = stage_landmarks(guide, N, rho, p, landmarks, w, L, false, f, H, W, n, st);
+  }
+  if (s != NYF_OK) return s;
+  const float* lm = reinterpret_cast<const float*>(w + L.landmarks);
+  float* what = reinterpret_cast<float*>(w + L.what);
+  void* phi = w + L.phi;
+  {
+    Stage t(st, 1);
+    NYF_TRY(launch_eig(lm, p->K, rho, p->sigma_r, p->eig_rel_tol, what, nullptr, nullptr, state, st));
+  }
+  {
+    Stage t(st, 2);
+    NYF_TRY(launch_features(guide, N, rho, lm, p->K, p->sigma_r, what, state, phi, bf16, st));
+  }
+  {
+    Stage t(st, 3);
+    NYF_TRY(launch_conv_combine(f, H, W, n, phi, bf16, p->spatial, p->sigma_s, window_radius(p),
+                                state, out, reinterpret_cast<float*>(w + L.eta),
+                                reinterpret_cast<float*>(w + L.zeta), st));
+  }
+  return NYF_OK;
+}
+
+nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params* p,
+                          const float* landmarks, float* out, void* ws, size_t ws_bytes,
+                          void* stream) {
+  if (!p || p->patch_radius < 0 || p->patch_radius > 8) return NYF_ERR_INVALID_ARG;
+  const int rho = nlm_rho(n, p->patch_radius);
+  nyf_status s = check_filter(f, H, W, n, rho, p, out);
+  if (s != NYF_OK) return s;
+  if (features_nlm_smem_bytes(p->K, n, p->patch_radius) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
+  const WsLayout L = ws_layout(shape_for(H, W, n, rho, p));
+  if (!ws_ok(ws, ws_bytes, L.total)) return NYF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  DevState* state = reinterpret_cast<DevState*>(w + L.state);
+  const bool bf16 = p->precision == NYF_BF16;
+  NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
+  // The patch guide is never stored: k-means always clusters a gathered
+  // subsample of patch vectors (all pixels when sample_frac == 1).
+  const int64_t N = (int64_t)H * W;
+  timing_begin(0, 3);
+  {
+    Stage t(st, 0);
+    s = stage_landmarks(nullptr, N, rho, p, landmarks, w, L, true, f, H, W, n, st);
+  }
+  if (s != NYF_OK) return s;
+  const float* lm = reinterpret_cast<const float*>(w + L.landmarks);
+  float* what = reinterpret_cast<float*>(w + L.what);
+  void* phi = w + L.phi;
+  {
+    Stage t(st, 1);
+    NYF_TRY(launch_eig(lm, p->K, rho, p->sigma_r, p->eig_rel_tol, what, nullptr, nullptr, state, st));
+  }
+  {
+    Stage t(st, 2);
+    NYF_TRY(launch_features_nlm(f, H, W, n, p->patch_radius, lm, p->K, p->sigma_r, what, state,
+                                phi, bf16, st));
+  }
+  {
+    Stage t(st, 3);
+    NYF_TRY(launch_conv_combine(f, H, W, n, phi, bf16, p->spatial, p->sigma_s, window_radius(p),
+                                state, out, reinterpret_cast<float*>(w + L.eta),
+                                reinterpret_cast<float*>(w + L.zeta), st));
+  }
+  return NYF_OK;
+}
+
+nyf_status nyf_filter_blf_backward(const float* f, const float* guide, int H, int W, int n,
+                                   int rho, const nyf_params* p, const float* out,
+                                   const float* grad_out, float* grad_f, float* grad_guide,
+                                   float* grad_sigma, void* ws, size_t ws_bytes, void* stream) {
+  (void)f; (void)guide; (void)H; (void)W; (void)n; (void)rho; (void)p; (void)out;
+  (void)grad_out; (void)grad_f; (void)grad_guide; (void)grad_sigma; (void)ws; (void)ws_bytes;
+  (void)stream;
+  return NYF_ERR_UNSUPPORTED;
+}
+
+nyf_status nyf_get_stats(const void* ws, nyf_stats* out, void* stream) {
+  if (!ws || !out) return NYF_ERR_INVALID_ARG;
+  DevState h;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(&h, ws, sizeof(DevState), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return NYF_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return NYF_ERR_CUDA;
+  memset(out, 0, sizeof(*out));
+  out->status = h.status;
+  out->rank = h.rank;
+  out->qerr = h.qerr;
+  out->alpha_max = h.alpha[0];
+  out->alpha_min_kept = h.rank > 0 ? h.alpha[h.rank - 1] : 0.0;
+  out->eta_small = (long long)h.eta_small;
+  out->grad_sigma_r = h.grad_sigma[0];
+  out->grad_sigma_s = h.grad_sigma[1];
+  return NYF_OK;
+}
+
+}  // extern "C"

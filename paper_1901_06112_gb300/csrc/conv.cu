@@ -1,0 +1,77 @@
+// Host side of the fused convolution + combine stage: radius selection, the
+// split-quantity epilogue (g_hat = zeta / eta when the n + 1 quantities do not
+// fit one CTA) and the launch.
+#include <math.h>
+
+#include "conv_impl.cuh"
+
+namespace nyf {
+namespace {
+
+__global__ void k_divide(const float* __restrict__ zeta, const float* __restrict__ eta, int64_t N,
+                         int n, float thr, float* __restrict__ out, DevState* state) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N * n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pix = i / n;
+    const float e = eta[pix];
+    out[i] = zeta[i] / e;
+    if (i % n == 0 && !(e > thr)) atomicAdd(&state->eta_small, 1ull);
+  }
+}
+
+}  // namespace
+
+// Smallest compiled radius >= S.
+int conv_compiled_radius(int S) {
+  if (S <= 16) return S < 1 ? 1 : S;
+  static const int big[] = {18, 20, 22, 24, 28, 32};
+  for (int v : big)
+    if (S <= v) return v;
+  return -1;
+}
+
+int conv_nq(int Sc) { return Sc <= 24 ? 4 : 2; }
+
+bool conv_split(int S, int n) {
+  const int Sc = conv_compiled_radius(S);
+  return n + 1 > conv_nq(Sc);
+}
+
+cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void* phi, bool bf16,
+                                int spatial, float sigma_s, int S, DevState* state, float* out,
+                                float* eta_out, float* zeta_ws, cudaStream_t st) {
+  const int Sc = conv_compiled_radius(S);
+  if (Sc < 0) return cudaErrorInvalidValue;
+  ConvArgs a;
+  a.f = f;
+  a.H = H;
+  a.W = W;
+  a.n = n;
+  a.N = (int64_t)H * W;
+  a.phi = phi;
+  a.bf16 = bf16 ? 1 : 0;
+  a.state = state;
+  a.state_rw = state;
+  a.box = spatial == NYF_BOX ? 1 : 0;
+  a.inv2s2 = a.box ? 0.f : (float)(1.0 / (2.0 * (double)sigma_s * (double)sigma_s));
+  a.S_true = S;
+  double mass = 0.0;   // full-window mass of omega
+  for (int z = -S; z <= S; ++z) mass += a.box ? 1.0 : exp(-(double)z * z * a.inv2s2);
+  a.eta_thr = (float)(1e-6 * mass * mass);
+  const bool split = n + 1 > conv_nq(Sc);
+  a.out = split ? nullptr : out;
+  a.zeta = split ? zeta_ws : nullptr;
+  a.eta = eta_out;
+  cudaError_t e;
+  if (Sc <= 8) e = conv_dispatch_a(Sc, a, st);
+  else if (Sc <= 16) e = conv_dispatch_b(Sc, a, st);
+  else e = conv_dispatch_c(Sc, a, st);
+  if (e != cudaSuccess || !split) return e;
+  int64_t g = (a.N * n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  k_divide<<<(int)g, 256, 0, st>>>(zeta_ws, eta_out, a.N, n, a.eta_thr, out, state);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace nyf

@@ -1,0 +1,348 @@
+// k-means landmark selection (Sec. III; Algorithm 1, clustering step) and the
+// NLM subsample gather.
+//
+// One Lloyd iteration = k_assign (nearest centroid of every row, ties to the
+// lowest index, plus per-block partial sums of the members of each cluster)
+// followed by k_update (one CTA per cluster sums the partials in FP64 and moves
+// the centroid to the mean; an empty cluster keeps its centroid).  Every
+// reduction runs in a fixed order, so the result is bitwise reproducible.
+#include "nyf_internal.cuh"
+
+namespace nyf {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+constexpr int assign_threads(int RB) { return RB > 0 ? 256 : 128; }
+
+// BLF subsample: stratum t of the row order gives row
+// lo + SplitMix64(seed ^ kSampleStream, t + 1) mod (hi - lo); it is copied to X.
+__global__ void k_sample_rows(const float* __restrict__ G, int64_t N, int rho, int64_t Ns,
+                              uint64_t seed, int64_t* __restrict__ idx, float* __restrict__ X) {
+  const int64_t total = Ns * rho;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / rho;
+    const int j = (int)(e - t * rho);
+    const int64_t lo = (int64_t)(((unsigned __int128)t * N) / Ns);
+    const int64_t hi = (int64_t)(((unsigned __int128)(t + 1) * N) / Ns);
+    const int64_t row = lo + (int64_t)(splitmix64(seed ^ kSampleStream, (uint64_t)t + 1) %
+                                       (uint64_t)(hi - lo));
+    if (j == 0) idx[t] = row;
+    X[e] = G[row * rho + j];
+  }
+}
+
+size_t assign_smem(int K, int rho) {
+  const int warps = assign_threads(rho <= 32 ? 1 : 0) / 32;
+  return sizeof(float) * ((size_t)K * rho + (size_t)warps * K * (rho + 1));
+}
+
+int kmeans_grid(int64_t N, int rho) {
+  const int64_t t = assign_threads(rho <= 32 ? 1 : 0);
+  const int64_t g = (N + t - 1) / t;
+  return (int)(g < kKmeansBlocks ? (g < 1 ? 1 : g) : kKmeansBlocks);
+}
+
+__device__ inline int reflect101(int i, int n) {
+  if (n == 1) return 0;
+  const int period = 2 * (n - 1);
+  int j = i % period;
+  if (j < 0) j += period;
+  return j < n ? j : period - j;
+}
+
+// Initial centroids: rows init_idx[j] of X, or the first K distinct values of
+// SplitMix64(seed) mod N (bounded number of draws).
+__global__ void k_draw_init(const float* __restrict__ X, int64_t N, int rho, int K, uint64_t seed,
+                            const int64_t* __restrict__ init_idx, int64_t* __restrict__ idx_out,
+                            float* __restrict__ cent, DevState* state) {
+  __shared__ int64_t idx[kMaxK];
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    if (init_idx) {
+      for (int j = 0; j < K; ++j) {
+        int64_t v = init_idx[j];
+        if (v < 0 || v >= N) { ok = 0; v = 0; }
+        idx[j] = v;
+      }
+      if (!ok) set_status(state, NYF_ERR_INVALID_ARG);
+    } else {
+      int cnt = 0;
+      const uint64_t max_draws = 64ull * (uint64_t)K + 4096ull;
+      for (uint64_t t = 1; t <= max_draws && cnt < K; ++t) {
+        const int64_t c = (int64_t)(splitmix64(seed, t) % (uint64_t)N);
+        bool dup = false;
+        for (int q = 0; q < cnt; ++q) dup |= (idx[q] == c);
+        if (!dup) idx[cnt++] = c;
+      }
+      if (cnt < K) {
+        ok = 0;
+        for (int q = cnt; q < K; ++q) idx[q] = 0;
+        set_status(state, NYF_ERR_TIMEOUT);
+      }
+    }
+    for (int j = 0; j < K; ++j) idx_out[j] = idx[j];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < K * rho; e += blockDim.x) {
+    const int j = e / rho, d = e - j * rho;
+    cent[e] = X[idx[j] * rho + d];
+  }
+}
+
+// Assignment pass.  RB > 0: the row is held in registers (rho <= RB); RB == 0:
+// it is re-read from global memory (large rho, used for small row counts).
+// part[b][j][0..rho) = sum of the members of cluster j seen by block b,
+// part[b][j][rho] = their count; qpart[b] = sum of their squared distances.
+template <int RB, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __restrict__ cent,
+         int32_t* __restrict__ labels, float* __restrict__ part, float* __restrict__ qpart,
+         int accumulate) {
+  extern __shared__ float sm[];
+  constexpr int kWarps = THREADS / 32;
+  float* mu = sm;                       // K * rho
+  float* acc = sm + K * rho;            // kWarps * K * (rho + 1)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int stride = rho + 1;
+  for (int e = tid; e < K * rho; e += blockDim.x) mu[e] = cent[e];
+  if (accumulate)
+    for (int e = tid; e < kWarps * K * stride; e += blockDim.x) acc[e] = 0.f;
+  __syncthreads();
+
+  float qsum = 0.f;
+  for (int64_t base = (int64_t)blockIdx.x * THREADS; base < N;
+       base += (int64_t)gridDim.x * THREADS) {
+    const int64_t i = base + tid;
+    const bool valid = i < N;
+    const float* xi = X + (valid ? i : 0) * rho;
+    float x[RB > 0 ? RB : 1];
+    if (RB > 0) {
+#pragma unroll
+      for (int d = 0; d < (RB > 0 ? RB : 1); ++d) x[d] = (d < rho) ? __ldg(xi + d) : 0.f;
+    }
+    int best = 0;
+    float bd = __int_as_float(0x7f800000);
+    for (int j = 0; j < K; ++j) {
+      const float* m = mu + j * rho;
+      float dist = 0.f;
+      if (RB > 0) {
+#pragma unroll
+        for (int d = 0; d < (RB > 0 ? RB : 1); ++d) {
+          if (d < rho) {
+            const float t = x[d] - m[d];
+            dist = fmaf(t, t, dist);
+          }
+        }
+      } else {
+        for (int d = 0; d < rho; ++d) {
+          const float t = __ldg(xi + d) - m[d];
+          dist = fmaf(t, t, dist);
+        }
+      }
+      if (dist < bd) { bd = dist; best = j; }   // strict: ties keep the lowest index
+    }
+    if (valid) {
+      qsum += bd;
+      if (labels) labels[i] = best;
+    }
+    if (accumulate) {
+      unsigned todo = __ballot_sync(kFull, valid);
+      while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int L = __shfl_sync(kFull, best, leader);
+        const bool mine = valid && best == L;
+        const unsigned grp = __ballot_sync(kFull, mine);
+        float* a = acc + (warp * K + L) * stride;
+        if (RB > 0) {
+#pragma unroll
+          for (int d = 0; d < (RB > 0 ? RB : 1); ++d) {
+            if (d < rho) {
+              const float v = warp_sum(mine ? x[d] : 0.f);
+              if (lane == 0) a[d] += v;
+            }
+          }
+        } else {
+          for (int d = 0; d < rho; ++d) {
+            const float v = warp_sum(mine ? __ldg(xi + d) : 0.f);
+            if (lane == 0) a[d] += v;
+          }
+        }
+        if (lane == 0) a[rho] += (float)__popc(grp);
+        todo &= ~grp;
+      }
+    }
+  }
+  __syncthreads();
+  if (accumulate) {
+    for (int e = tid; e < K * stride; e += blockDim.x) {
+      float s = 0.f;
+      for (int w = 0; w < kWarps; ++w) s += acc[w * K * stride + e];
+      part[(int64_t)blockIdx.x * K * stride + e] = s;
+    }
+  }
+  __shared__ float qs[kWarps];
+  qsum = warp_sum(qsum);
+  if (lane == 0) qs[warp] = qsum;
+  __syncthreads();
+  if (tid == 0) {
+    float s = 0.f;
+    for (int w = 0; w < kWarps; ++w) s += qs[w];
+    qpart[blockIdx.x] = s;
+  }
+}
+
+// One CTA per cluster j: FP64 sums of the block partials in a fixed order, then
+// the centroid moves to the mean of its members (kept if it has none).
+__global__ void __launch_bounds__(256)
+k_update(const float* __restrict__ part, int nblk, int rho, int K, float* __restrict__ cent) {
+  __shared__ double red[256];
+  __shared__ double cnt;
+  const int j = blockIdx.x, tid = threadIdx.x, stride = rho + 1;
+  for (int d = rho; d >= 0; --d) {       // count (d == rho) first
+    double s = 0.0;
+    for (int b = tid; b < nblk; b += 256) s += (double)part[((int64_t)b * K + j) * stride + d];
+    red[tid] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (tid < o) red[tid] += red[tid + o];
+      __syncthreads();
+    }
+    if (tid == 0) {
+      if (d == rho) cnt = red[0];
+      else if (cnt > 0.0) cent[j * rho + d] = (float)(red[0] / cnt);
+    }
+    __syncthreads();
+  }
+}
+
+// Quantisation error e = sum of the block partials (FP64, fixed order).
+__global__ void k_qerr(const float* __restrict__ qpart, int nblk, double* __restrict__ out,
+                       DevState* state) {
+  __shared__ double red[256];
+  const int tid = threadIdx.x;
+  double s = 0.0;
+  for (int b = tid; b < nblk; b += 256) s += (double)qpart[b];
+  red[tid] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (tid < o) red[tid] += red[tid + o];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    state->qerr = red[0];
+    if (out) *out = red[0];
+  }
+}
+
+// NLM subsample: stratum t of the row-major pixel order gives pixel
+// lo + SplitMix64(seed ^ kSampleStream, t + 1) mod (hi - lo); its patch vector
+// (reflect-101 border, order (dy, dx, c)) becomes row t of X.
+__global__ void k_nlm_sample(const float* __restrict__ f, int H, int W, int n, int r, int64_t Ns,
+                             uint64_t seed, int64_t* __restrict__ idx, float* __restrict__ X) {
+  const int side = 2 * r + 1;
+  const int rho = side * side * n;
+  const int64_t N = (int64_t)H * W;
+  const int64_t total = Ns * rho;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / rho;
+    const int j = (int)(e - t * rho);
+    const int64_t lo = (int64_t)(((unsigned __int128)t * N) / Ns);
+    const int64_t hi = (int64_t)(((unsigned __int128)(t + 1) * N) / Ns);
+    const int64_t pix = lo + (int64_t)(splitmix64(seed ^ kSampleStream, (uint64_t)t + 1) %
+                                       (uint64_t)(hi - lo));
+    if (j == 0) idx[t] = pix;
+    const int c = j % n;
+    const int q = j / n;
+    const int dy = q / side - r, dx = q % side - r;
+    const int y = (int)(pix / W), x = (int)(pix % W);
+    X[e] = f[((int64_t)reflect101(y + dy, H) * W + reflect101(x + dx, W)) * n + c];
+  }
+}
+
+template <int RB>
+cudaError_t assign_launch(int grid, const float* X, int64_t N, int rho, int K, const float* cent,
+                          int32_t* labels, float* part, float* qpart, int accumulate,
+                          cudaStream_t st) {
+  constexpr int T = assign_threads(RB);
+  const size_t smem = assign_smem(K, rho);
+  cudaError_t e = cudaFuncSetAttribute(k_assign<RB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_assign<RB, T><<<grid, T, smem, st>>>(X, N, rho, K, cent, labels, part, qpart, accumulate);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t assign_dispatch(int grid, const float* X, int64_t N, int rho, int K,
+                            const float* cent, int32_t* labels, float* part, float* qpart,
+                            int accumulate, cudaStream_t st) {
+  if (rho <= 4) return assign_launch<4>(grid, X, N, rho, K, cent, labels, part, qpart, accumulate, st);
+  if (rho <= 8) return assign_launch<8>(grid, X, N, rho, K, cent, labels, part, qpart, accumulate, st);
+  if (rho <= 16) return assign_launch<16>(grid, X, N, rho, K, cent, labels, part, qpart, accumulate, st);
+  if (rho <= 32) return assign_launch<32>(grid, X, N, rho, K, cent, labels, part, qpart, accumulate, st);
+  return assign_launch<0>(grid, X, N, rho, K, cent, labels, part, qpart, accumulate, st);
+}
+
+}  // namespace
+
+size_t kmeans_smem_bytes(int K, int rho) { return assign_smem(K, rho); }
+
+cudaError_t launch_draw_init(const float* X, int64_t N, int rho, int K, uint64_t seed,
+                             const int64_t* init_idx, int64_t* idx_out, float* centroids,
+                             DevState* state, cudaStream_t st) {
+  k_draw_init<<<1, 256, 0, st>>>(X, N, rho, K, seed, init_idx, idx_out, centroids, state);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kmeans(const float* X, int64_t N, int rho, int K, int iters, float* centroids,
+                          int32_t* labels, double* qerr_out, float* part, float* qpart,
+                          DevState* state, cudaStream_t st) {
+  const int grid = kmeans_grid(N, rho);
+  for (int it = 0; it < iters; ++it) {
+    cudaError_t e = assign_dispatch(grid, X, N, rho, K, centroids, nullptr, part, qpart, 1, st);
+    if (e != cudaSuccess) return e;
+    k_update<<<K, 256, 0, st>>>(part, grid, rho, K, centroids);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  cudaError_t e = assign_dispatch(grid, X, N, rho, K, centroids, labels, part, qpart, 0, st);
+  if (e != cudaSuccess) return e;
+  k_qerr<<<1, 256, 0, st>>>(qpart, grid, qerr_out, state);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_rows(const float* guide, int64_t N, int rho, int64_t Ns, uint64_t seed,
+                               int64_t* idx, float* X, cudaStream_t st) {
+  int64_t grid = (Ns * rho + 255) / 256;
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  k_sample_rows<<<(int)grid, 256, 0, st>>>(guide, N, rho, Ns, seed, idx, X);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nlm_sample(const float* f, int H, int W, int n, int r, int64_t Ns, uint64_t seed,
+                              int64_t* idx, float* X, cudaStream_t st) {
+  const int rho = (2 * r + 1) * (2 * r + 1) * n;
+  const int64_t total = Ns * rho;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  k_nlm_sample<<<grid, 256, 0, st>>>(f, H, W, n, r, Ns, seed, idx, X);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace nyf

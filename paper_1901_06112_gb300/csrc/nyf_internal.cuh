@@ -1,0 +1,100 @@
+// Internal declarations shared by the libnyf translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/nyf.h"
+
+namespace nyf {
+
+constexpr int kMaxK = NYF_MAX_K;
+constexpr int kMaxRho = NYF_MAX_RHO;
+constexpr int kMaxS = NYF_MAX_S;
+constexpr int kMaxChannels = NYF_MAX_CHANNELS;
+constexpr int kKmeansBlocks = 1216;      // 8 x 152 SMs: partial-sum slots of the assign pass
+constexpr int kKmeansThreads = 256;
+
+// Device-side state at the start of every workspace.
+struct DevState {
+  int status;                 // sticky nyf_status
+  int rank;                   // kept modes r
+  unsigned long long eta_small;
+  double qerr;
+  double alpha[kMaxK];        // eigenvalues of A, descending
+  float grad_sigma[2];
+  int pad[2];
+};
+
+// Byte offsets of every region of a workspace (all 256-byte aligned).
+struct WsLayout {
+  size_t state, landmarks, what, init_idx, km_part, km_qpart, sample_idx, sample_x, phi, eta,
+      zeta, dphi, gpart, total;
+};
+
+// Problem geometry used to size a workspace.
+struct WsShape {
+  int64_t N;        // pixels (rows of the guide)
+  int n;            // image channels
+  int rho;          // guide dimension
+  int K;            // landmarks
+  int64_t Ns;       // rows k-means clusters
+  bool bf16;        // features stored as bfloat16
+  bool gather;      // k-means rows are gathered (subsample or NLM patches)
+};
+
+WsLayout ws_layout(const WsShape& s);
+
+__host__ __device__ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Sticky error latch: the first error wins.
+__device__ inline void set_status(DevState* st, int code) { atomicCAS(&st->status, 0, code); }
+
+// ---- SplitMix64 (Steele, Lea & Flood 2014): output t of the stream seeded with s.
+__host__ __device__ inline uint64_t splitmix64(uint64_t seed, uint64_t t) {
+  uint64_t z = seed + t * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+constexpr uint64_t kSampleStream = 0xA5A5A5A5A5A5A5A5ull;
+
+// Host-side count of kernel launches (nyf_launch_count).
+void count_launches(int k);
+
+// ---- launchers (one per kernel family); all enqueue on `st` and return a cudaError_t.
+cudaError_t launch_draw_init(const float* X, int64_t N, int rho, int K, uint64_t seed,
+                             const int64_t* init_idx, int64_t* idx_out, float* centroids,
+                             DevState* state, cudaStream_t st);
+cudaError_t launch_kmeans(const float* X, int64_t N, int rho, int K, int iters, float* centroids,
+                          int32_t* labels, double* qerr_out, float* part, float* qpart,
+                          DevState* state, cudaStream_t st);
+cudaError_t launch_sample_rows(const float* guide, int64_t N, int rho, int64_t Ns, uint64_t seed,
+                               int64_t* idx, float* X, cudaStream_t st);
+size_t kmeans_smem_bytes(int K, int rho);
+cudaError_t launch_nlm_sample(const float* f, int H, int W, int n, int r, int64_t Ns, uint64_t seed,
+                              int64_t* idx, float* X, cudaStream_t st);
+cudaError_t launch_eig(const float* landmarks, int K, int rho, float sigma_r, double tau,
+                       float* what, double* alphas_out, int* rank_out, DevState* state,
+                       cudaStream_t st);
+cudaError_t launch_features(const float* guide, int64_t N, int rho, const float* landmarks, int K,
+                            float sigma_r, const float* what, const DevState* state, void* phi,
+                            bool bf16, cudaStream_t st);
+cudaError_t launch_features_nlm(const float* f, int H, int W, int n, int r, const float* landmarks,
+                                int K, float sigma_r, const float* what, const DevState* state,
+                                void* phi, bool bf16, cudaStream_t st);
+size_t features_nlm_smem_bytes(int K, int n, int r);
+cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void* phi, bool bf16,
+                                int spatial, float sigma_s, int S, DevState* state, float* out,
+                                float* eta_out, float* zeta_ws, cudaStream_t st);
+int conv_compiled_radius(int S);
+bool conv_split(int S, int n);
+cudaError_t launch_backward(const float* f, const float* guide, int H, int W, int n, int rho,
+                            const float* landmarks, int K, float sigma_r, int spatial,
+                            float sigma_s, int S, const float* what, const void* phi, bool bf16,
+                            const float* eta, const float* out, const float* grad_out,
+                            float* grad_f, float* grad_guide, float* dphi, float* gpart,
+                            float* grad_sigma, DevState* state, cudaStream_t st);
+
+}  // namespace nyf

@@ -1,0 +1,168 @@
+"""Python entry points of the GB300 Nystrom kernel filter.
+
+Each function checks and marshals torch CUDA tensors into the C ABI of
+libnyf (include/nyf.h) and enqueues the work on the current CUDA stream.
+PyTorch supplies device memory and streams only; every step of the method
+runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as L
+
+
+@dataclass
+class Params:
+    """Filter parameters (see nyf_params in include/nyf.h)."""
+
+    sigma_s: float = 3.0
+    sigma_r: float = 30.0
+    K: int = 8
+    kmeans_iters: int = 10
+    seed: int = 0
+    eig_rel_tol: float = 1e-7
+    precision: str = "fp32"        # "fp32" | "bf16": storage of the per-pixel features
+    spatial: str = "gaussian"      # "gaussian" | "box"
+    S: int = 0                     # window radius; 0 -> ceil(3 sigma_s)
+    patch_radius: int = 0          # NLM patch radius
+    sample_frac: float = 1.0
+
+    def c(self) -> L.NyfParams:
+        return L.NyfParams(float(self.sigma_s), float(self.sigma_r), int(self.K),
+                           int(self.kmeans_iters), int(self.seed) & ((1 << 64) - 1),
+                           float(self.eig_rel_tol),
+                           L.BF16 if self.precision == "bf16" else L.FP32,
+                           L.BOX if self.spatial == "box" else L.GAUSSIAN, int(self.S),
+                           int(self.patch_radius), float(self.sample_frac))
+
+    @property
+    def radius(self) -> int:
+        return self.S if self.S > 0 else int(math.ceil(3.0 * self.sigma_s))
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check_image(t, name, channels=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if channels is not None and (t.dim() != 3 or t.shape[2] != channels):
+        raise ValueError(f"{name} must be H x W x {channels}")
+
+
+class Workspace:
+    """A 256-byte aligned device buffer of at least `nbytes` bytes."""
+
+    def __init__(self, nbytes: int, device):
+        self.buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        self.ptr = self.buf.data_ptr() + off
+        self.nbytes = int(nbytes)
+
+    def cptr(self):
+        return C.c_void_p(self.ptr)
+
+
+def workspace_size(H, W, n, rho, params: Params) -> int:
+    lib = L.load()
+    p = params.c()
+    s = lib.nyf_workspace_size(H, W, n, rho, C.byref(p))
+    if s == 0:
+        raise ValueError("invalid sizes or parameters for nyf_workspace_size")
+    return int(s)
+
+
+def make_workspace(H, W, n, rho, params: Params, device="cuda") -> Workspace:
+    return Workspace(workspace_size(H, W, n, rho, params), device)
+
+
+def blf(f, params: Params, guide=None, landmarks=None, out=None, ws: Workspace | None = None):
+    """Nystrom bilateral filter (Algorithm 1): returns g_hat (H x W x n)."""
+    lib = L.load()
+    _check_image(f, "f")
+    H, W, n = f.shape
+    rho = n
+    if guide is not None:
+        _check_image(guide, "guide")
+        if guide.shape[:2] != f.shape[:2]:
+            raise ValueError("guide must have the image's H x W")
+        rho = guide.shape[2]
+    if landmarks is not None:
+        if not (landmarks.is_cuda and landmarks.dtype == torch.float32 and landmarks.is_contiguous()
+                and landmarks.shape == (params.K, rho)):
+            raise ValueError("landmarks must be a contiguous float32 CUDA tensor of K x rho")
+    out = torch.empty_like(f) if out is None else out
+    ws = ws or make_workspace(H, W, n, rho, params, f.device)
+    p = params.c()
+    L.check(lib.nyf_filter_blf(_ptr(f), _ptr(guide), H, W, n, rho, C.byref(p), _ptr(landmarks),
+                               _ptr(out), ws.cptr(), ws.nbytes, _stream()), "nyf_filter_blf")
+    return out
+
+
+def nlm(f, params: Params, landmarks=None, out=None, ws: Workspace | None = None):
+    """Nystrom nonlocal means (patch guide, box window): returns g_hat."""
+    lib = L.load()
+    _check_image(f, "f")
+    H, W, n = f.shape
+    out = torch.empty_like(f) if out is None else out
+    rho = n * (2 * params.patch_radius + 1) ** 2
+    ws = ws or make_workspace(H, W, n, rho, params, f.device)
+    p = params.c()
+    L.check(lib.nyf_filter_nlm(_ptr(f), H, W, n, C.byref(p), _ptr(landmarks), _ptr(out), ws.cptr(),
+                               ws.nbytes, _stream()), "nyf_filter_nlm")
+    return out
+
+
+def kmeans(X, K, iters=10, seed=0, init_idx=None, ws: Workspace | None = None):
+    """k-means landmarks of the rows of X (N x rho): (centroids, labels, qerr)."""
+    lib = L.load()
+    if not (X.is_cuda and X.dtype == torch.float32 and X.is_contiguous() and X.dim() == 2):
+        raise TypeError("X must be a contiguous float32 CUDA tensor of N x rho")
+    N, rho = X.shape
+    cent = torch.empty((K, rho), dtype=torch.float32, device=X.device)
+    labels = torch.empty(N, dtype=torch.int32, device=X.device)
+    qerr = torch.empty(1, dtype=torch.float64, device=X.device)
+    if init_idx is not None:
+        init_idx = init_idx.to(device=X.device, dtype=torch.int64).contiguous()
+    ws = ws or make_workspace(N, 1, rho, rho, Params(K=K))
+    L.check(lib.nyf_kmeans(_ptr(X), N, rho, K, iters, int(seed) & ((1 << 64) - 1),
+                           _ptr(init_idx), _ptr(cent), _ptr(labels), _ptr(qerr), ws.cptr(),
+                           ws.nbytes, _stream()), "nyf_kmeans")
+    return cent, labels, qerr
+
+
+def features(guide2d, landmarks, sigma_r, eig_rel_tol=1e-7, precision="fp32",
+             ws: Workspace | None = None):
+    """Per-pixel Nystrom features: (phi K x N, rank, alphas)."""
+    lib = L.load()
+    N, rho = guide2d.shape
+    K = landmarks.shape[0]
+    dt = torch.bfloat16 if precision == "bf16" else torch.float32
+    phi = torch.zeros((K, N), dtype=dt, device=guide2d.device)
+    rank = torch.zeros(1, dtype=torch.int32, device=guide2d.device)
+    alphas = torch.zeros(K, dtype=torch.float64, device=guide2d.device)
+    ws = ws or make_workspace(N, 1, rho, rho, Params(K=K, precision=precision))
+    L.check(lib.nyf_features(_ptr(guide2d), N, rho, _ptr(landmarks), K, float(sigma_r),
+                             float(eig_rel_tol), L.BF16 if precision == "bf16" else L.FP32,
+                             _ptr(phi), _ptr(rank), _ptr(alphas), ws.cptr(), ws.nbytes,
+                             _stream()), "nyf_features")
+    return phi, rank, alphas
+
+
+def stats(ws: Workspace) -> dict:
+    """Device-side results of the last call on `ws` (synchronises the stream)."""
+    lib = L.load()
+    s = L.NyfStats()
+    L.check(lib.nyf_get_stats(ws.cptr(), C.byref(s), _stream()), "nyf_get_stats")
+    return {k: getattr(s, k) for k, _ in L.NyfStats._fields_}

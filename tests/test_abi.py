@@ -1,0 +1,65 @@
+"""The C-ABI library builds, loads and exports every symbol include/nyf.h declares (no GPU calls)."""
+import ctypes as C
+import os
+
+import pytest
+
+from paper_1901_06112_gb300 import _lib, build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _lib.declared_symbols()
+    assert {"nyf_kmeans", "nyf_features", "nyf_filter_blf", "nyf_filter_nlm",
+            "nyf_filter_blf_backward", "nyf_workspace_size", "nyf_get_stats"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings_and_version(lib):
+    assert lib.nyf_version() >= 100
+    for code in range(7):
+        assert lib.nyf_status_string(code)
+
+
+def test_workspace_size_host_logic(lib):
+    p = _lib.NyfParams(3.0, 30.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0)
+    s1 = lib.nyf_workspace_size(256, 256, 3, 3, C.byref(p))
+    s2 = lib.nyf_workspace_size(512, 256, 3, 3, C.byref(p))
+    assert s1 > 0 and s2 > s1
+    p.precision = 1
+    assert lib.nyf_workspace_size(256, 256, 3, 3, C.byref(p)) < s1     # bf16 features are smaller
+    p.K = 0
+    assert lib.nyf_workspace_size(256, 256, 3, 3, C.byref(p)) == 0
+    p.K = 8
+    p.patch_radius = 2        # NLM: rho is derived from n and r
+    assert lib.nyf_workspace_size(64, 64, 3, 1, C.byref(p)) > 0
+
+
+def test_argument_errors_return_before_any_launch(lib):
+    p = _lib.NyfParams(3.0, 30.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0)
+    bad = C.c_void_p(256)
+    # null image
+    assert lib.nyf_filter_blf(None, None, 8, 8, 3, 3, C.byref(p), None, bad, bad, 1 << 20, None) == 1
+    # negative sigma_r
+    q = _lib.NyfParams(3.0, -1.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0)
+    assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(q), None, bad, bad, 1 << 20, None) == 1
+    # too many landmarks
+    q = _lib.NyfParams(3.0, 30.0, 65, 10, 0, 1e-7, 0, 0, 0, 0, 1.0)
+    assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(q), None, bad, bad, 1 << 20, None) == 1
+    # window radius beyond the compiled maximum
+    q = _lib.NyfParams(11.0, 30.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0)
+    assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(q), None, bad, bad, 1 << 20, None) == 2
+    # workspace too small / misaligned
+    assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(p), None, bad, bad, 16, None) == 3
+    assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(p), None, bad, C.c_void_p(260),
+                              1 << 30, None) == 3
+    # guide dimension must equal n when the guide is the image
+    assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 2, C.byref(p), None, bad, bad, 1 << 30, None) == 1
+    # k-means: more clusters than rows
+    assert lib.nyf_kmeans(bad, 4, 3, 8, 1, 0, None, bad, None, None, bad, 1 << 20, None) == 1
