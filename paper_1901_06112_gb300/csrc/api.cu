@@ -29,6 +29,7 @@ WsLayout ws_layout(const WsShape& s) {
   L.state = take(sizeof(DevState));
   L.landmarks = take(sizeof(float) * K * rho);
   L.what = take(sizeof(float) * K * K);
+  L.eig = take(eig_scratch_bytes());
   L.init_idx = take(sizeof(int64_t) * K);
   L.km_part = take(sizeof(float) * (size_t)kKmeansBlocks * K * (rho + 1));
   L.km_qpart = take(sizeof(float) * (size_t)kKmeansBlocks);
@@ -39,7 +40,9 @@ WsLayout ws_layout(const WsShape& s) {
   L.eta = take(sizeof(float) * N);
   L.zeta = take(sizeof(float) * N * (size_t)s.n);
   L.dphi = take(sizeof(float) * K * N);
-  L.gpart = take(sizeof(float) * (size_t)kKmeansBlocks * (K * K + K * rho + 8));
+  L.gpart = take(sizeof(float) * backward_gpart_floats(s.K));
+  L.spart = take(sizeof(float) * backward_spart_floats(s.H, s.W, s.n));
+  L.gw = take(sizeof(double) * K * K);
   L.total = o;
   return L;
 }
@@ -141,6 +144,8 @@ nyf_status check_filter(const float* f, int H, int W, int n, int rho, const nyf_
 
 WsShape shape_for(int H, int W, int n, int rho, const nyf_params* p) {
   WsShape s;
+  s.H = H;
+  s.W = W;
   s.N = (int64_t)H * W;
   s.n = n;
   s.rho = rho;
@@ -247,7 +252,7 @@ nyf_status nyf_kmeans(const float* X, int64_t N, int rho, int K, int iters, uint
       K < 1 || K > NYF_MAX_K || K > N || iters < 0)
     return NYF_ERR_INVALID_ARG;
   if (kmeans_smem_bytes(K, rho) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
-  WsShape s{N, 1, rho, K, N, false, false};
+  WsShape s{(int)N, 1, N, 1, rho, K, N, false, false};
   const WsLayout L = ws_layout(s);
   if (!ws_ok(ws, ws_bytes, L.km_qpart + sizeof(float) * kKmeansBlocks)) return NYF_ERR_WORKSPACE;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -270,15 +275,16 @@ nyf_status nyf_features(const float* guide, int64_t N, int rho, const float* lan
       !(eig_rel_tol >= 0.0) || (precision != NYF_FP32 && precision != NYF_BF16))
     return NYF_ERR_INVALID_ARG;
   if (sizeof(float) * ((size_t)K * rho + (size_t)K * K) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
-  WsShape s{N, 1, rho, K, N, precision == NYF_BF16, false};
+  WsShape s{(int)N, 1, N, 1, rho, K, N, precision == NYF_BF16, false};
   const WsLayout L = ws_layout(s);
-  if (!ws_ok(ws, ws_bytes, L.what + sizeof(float) * K * K)) return NYF_ERR_WORKSPACE;
+  if (!ws_ok(ws, ws_bytes, L.eig + eig_scratch_bytes())) return NYF_ERR_WORKSPACE;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = reinterpret_cast<char*>(ws);
   DevState* state = reinterpret_cast<DevState*>(w + L.state);
   float* what = reinterpret_cast<float*>(w + L.what);
   NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
-  NYF_TRY(launch_eig(landmarks, K, rho, sigma_r, eig_rel_tol, what, alphas, rank, state, st));
+  NYF_TRY(launch_eig(landmarks, K, rho, sigma_r, eig_rel_tol, what, alphas, rank, state, w + L.eig,
+                     st));
   NYF_TRY(launch_features(guide, N, rho, landmarks, K, sigma_r, what, state, phi,
                           precision == NYF_BF16, st));
   return NYF_OK;
@@ -314,7 +320,8 @@ nyf_status nyf_filter_blf(const float* f, const float* guide, int H, int W, int 
   void* phi = w + L.phi;
   {
     Stage t(st, 1);
-    NYF_TRY(launch_eig(lm, p->K, rho, p->sigma_r, p->eig_rel_tol, what, nullptr, nullptr, state, st));
+    NYF_TRY(launch_eig(lm, p->K, rho, p->sigma_r, p->eig_rel_tol, what, nullptr, nullptr, state,
+                       w + L.eig, st));
   }
   {
     Stage t(st, 2);
@@ -358,7 +365,8 @@ nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params*
   void* phi = w + L.phi;
   {
     Stage t(st, 1);
-    NYF_TRY(launch_eig(lm, p->K, rho, p->sigma_r, p->eig_rel_tol, what, nullptr, nullptr, state, st));
+    NYF_TRY(launch_eig(lm, p->K, rho, p->sigma_r, p->eig_rel_tol, what, nullptr, nullptr, state,
+                       w + L.eig, st));
   }
   {
     Stage t(st, 2);
@@ -378,10 +386,43 @@ nyf_status nyf_filter_blf_backward(const float* f, const float* guide, int H, in
                                    int rho, const nyf_params* p, const float* out,
                                    const float* grad_out, float* grad_f, float* grad_guide,
                                    float* grad_sigma, void* ws, size_t ws_bytes, void* stream) {
-  (void)f; (void)guide; (void)H; (void)W; (void)n; (void)rho; (void)p; (void)out;
-  (void)grad_out; (void)grad_f; (void)grad_guide; (void)grad_sigma; (void)ws; (void)ws_bytes;
-  (void)stream;
-  return NYF_ERR_UNSUPPORTED;
+  if (!p || p->patch_radius != 0) return NYF_ERR_INVALID_ARG;
+  const bool tied = guide == nullptr || guide == f;
+  if (tied) {
+    if (rho != n) return NYF_ERR_INVALID_ARG;
+    guide = f;
+  }
+  nyf_status s = check_filter(f, H, W, n, rho, p, out);
+  if (s != NYF_OK) return s;
+  if (!grad_out || !grad_f || !grad_sigma || !aligned4(grad_out) || !aligned4(grad_f) ||
+      !aligned4(grad_sigma) || (!tied && (!grad_guide || !aligned4(grad_guide))))
+    return NYF_ERR_INVALID_ARG;
+  const WsLayout L = ws_layout(shape_for(H, W, n, rho, p));
+  if (!ws_ok(ws, ws_bytes, L.total)) return NYF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  DevState* state = reinterpret_cast<DevState*>(w + L.state);
+  const bool bf16 = p->precision == NYF_BF16;
+  const int S = window_radius(p);
+  float* dphi = reinterpret_cast<float*>(w + L.dphi);
+  float* spart = reinterpret_cast<float*>(w + L.spart);
+  timing_begin(4, 6);
+  {
+    Stage t(st, 4);
+    NYF_TRY(launch_bwd_conv(f, H, W, n, p->K, p->spatial, p->sigma_s, S, w + L.phi, bf16,
+                            reinterpret_cast<const float*>(w + L.eta), out, grad_out, grad_f, dphi,
+                            spart, state, st));
+  }
+  {
+    Stage t(st, 5);
+    NYF_TRY(launch_bwd_features(f, guide, H, W, n, rho, reinterpret_cast<const float*>(w + L.landmarks),
+                                p->K, p->sigma_r, S, reinterpret_cast<const float*>(w + L.what),
+                                dphi, grad_f, tied ? nullptr : grad_guide,
+                                reinterpret_cast<float*>(w + L.gpart), spart,
+                                reinterpret_cast<double*>(w + L.gw), w + L.eig, grad_sigma, state,
+                                st));
+  }
+  return NYF_OK;
 }
 
 nyf_status nyf_get_stats(const void* ws, nyf_stats* out, void* stream) {

@@ -1,0 +1,385 @@
+// Backward of the features and the landmark-kernel factor (adjoint of
+// Eqs. (9)-(12)), and the host launcher of the whole backward pass.
+//
+// With E_im = exp(-D_im / (2 sigma_r^2)), D_im = ||p_i - mu_m||^2 and
+// Phi = E W_hat (W_hat = W_r Lambda_r^{-1/2}, so W_hat W_hat^T is the truncated
+// inverse of A):
+//   dE_im = sum_k dPhi_ik W_hat[m][k]
+//   dp_i  = sum_m (-E_im dE_im / (2 sigma_r^2)) 2 (p_i - mu_m)
+//   dsigma_r (through E) = sum_im dE_im E_im D_im / sigma_r^3
+// The filter depends on W_hat only through M = W_hat W_hat^T = A^+ (it sees
+// Phi Phi^T), so with G_W = E^T dPhi:  dL/dA = -1/2 W_hat (W_hat^T G_W) W_hat^T
+// (exact for full rank; for a truncated rank the rotation of the kept subspace
+// is not differentiated), and
+//   dsigma_r (through A) = sum_ij dL/dA_ij A_ij ||mu_i - mu_j||^2 / sigma_r^3.
+// Landmarks are held fixed.  All cross-block sums run in a fixed order in FP64.
+#include <math.h>
+
+#include "backward_impl.cuh"
+
+namespace nyf {
+namespace {
+
+constexpr int kFbBlocks = 304;      // features-backward CTAs (2 per SM)
+constexpr int kFbThreads = 256;
+
+__host__ __device__ inline int kpad4(int K) { return (K + 3) & ~3; }
+
+template <int KB, int RB>
+__global__ void __launch_bounds__(kFbThreads)
+k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float* __restrict__ lm,
+               int K, float inv2s2r, const float* __restrict__ what,
+               const DevState* __restrict__ state, const float* __restrict__ dphi,
+               float* __restrict__ dguide, int add_into, float* __restrict__ gw_part,
+               float* __restrict__ sr_part) {
+  extern __shared__ __align__(16) float sm[];
+  const int KP = kpad4(K);
+  float* Wsm = sm;                          // K x KP
+  float* mu = Wsm + K * KP;                 // K x rho
+  float* Es = mu + ((K * rho + 3) & ~3);    // kFbThreads x KB
+  float* Ds = Es + kFbThreads * KB;         // kFbThreads x KB
+  const int tid = threadIdx.x;
+  const int r = state->rank;
+  for (int e = tid; e < K * KP; e += blockDim.x) {
+    const int m = e / KP, k = e - m * KP;
+    Wsm[e] = k < K ? what[m * K + k] : 0.f;
+  }
+  for (int e = tid; e < K * rho; e += blockDim.x) mu[e] = lm[e];
+  // this thread's 2 x 2 blocks of G_W = E^T dPhi
+  constexpr int kMaxOwn = (KB / 2) * (KB / 2) / kFbThreads > 0 ? (KB / 2) * (KB / 2) / kFbThreads : 1;
+  float gw[kMaxOwn][4];
+#pragma unroll
+  for (int o = 0; o < kMaxOwn; ++o) gw[o][0] = gw[o][1] = gw[o][2] = gw[o][3] = 0.f;
+  float srp = 0.f;
+  __syncthreads();
+
+  for (int64_t base = (int64_t)blockIdx.x * kFbThreads; base < N;
+       base += (int64_t)gridDim.x * kFbThreads) {
+    const int64_t i = base + tid;
+    const bool valid = i < N;
+    const float* p = guide + (valid ? i : 0) * rho;
+    float x[RB > 0 ? RB : 1];
+    if (RB > 0) {
+#pragma unroll
+      for (int d = 0; d < (RB > 0 ? RB : 1); ++d) x[d] = (d < rho) ? __ldg(p + d) : 0.f;
+    }
+    float e[KB], d2[KB], g[KB];
+#pragma unroll
+    for (int m = 0; m < KB; ++m) {
+      float s = 0.f;
+      if (m < K) {
+        const float* c = mu + m * rho;
+        if (RB > 0) {
+#pragma unroll
+          for (int d = 0; d < (RB > 0 ? RB : 1); ++d)
+            if (d < rho) {
+              const float t = x[d] - c[d];
+              s = fmaf(t, t, s);
+            }
+        } else {
+          for (int d = 0; d < rho; ++d) {
+            const float t = __ldg(p + d) - c[d];
+            s = fmaf(t, t, s);
+          }
+        }
+      }
+      d2[m] = s;
+      e[m] = (m < K && valid) ? expf(-s * inv2s2r) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < KB; ++k) g[k] = (valid && k < r) ? dphi[(int64_t)k * N + i] : 0.f;
+    // dE_m = sum_k dPhi_k W_hat[m][k]; dD_m; sigma_r and guide terms
+    float dD[KB];
+#pragma unroll
+    for (int m = 0; m < KB; ++m) {
+      float de = 0.f;
+      if (m < K) {
+#pragma unroll
+        for (int k = 0; k < KB; k += 4) {
+          if (k < r) {
+            const float4 w = *reinterpret_cast<const float4*>(Wsm + m * KP + k);
+            de = fmaf(g[k], w.x, de);
+            if (k + 1 < KB) de = fmaf(g[k + 1 < KB ? k + 1 : k], w.y, de);
+            if (k + 2 < KB) de = fmaf(g[k + 2 < KB ? k + 2 : k], w.z, de);
+            if (k + 3 < KB) de = fmaf(g[k + 3 < KB ? k + 3 : k], w.w, de);
+          }
+        }
+      }
+      srp = fmaf(de * e[m], d2[m], srp);
+      dD[m] = -e[m] * de * inv2s2r;
+    }
+    if (valid) {
+      float* dst = dguide + i * rho;
+      for (int d = 0; d < rho; ++d) {
+        const float xd = RB > 0 ? 0.f : __ldg(p + d);
+        float s = 0.f;
+#pragma unroll
+        for (int m = 0; m < KB; ++m)
+          if (m < K) {
+            float xv = xd;
+            if (RB > 0) {
+#pragma unroll
+              for (int q = 0; q < (RB > 0 ? RB : 1); ++q) if (q == d) xv = x[q];
+            }
+            s = fmaf(dD[m], 2.f * (xv - mu[m * rho + d]), s);
+          }
+        dst[d] = add_into ? dst[d] + s : s;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < KB; ++m) {
+      Es[tid * KB + m] = e[m];
+      Ds[tid * KB + m] = g[m];
+    }
+    __syncthreads();
+    // G_W += E^T dPhi over this round's pixels
+    const int nb = (K + 1) / 2, rb = (r + 1) / 2;
+#pragma unroll
+    for (int o = 0; o < kMaxOwn; ++o) {
+      const int blk = tid + o * kFbThreads;
+      if (blk < nb * rb) {
+        const int m0 = 2 * (blk / rb), k0 = 2 * (blk % rb);
+        float s0 = gw[o][0], s1 = gw[o][1], s2 = gw[o][2], s3 = gw[o][3];
+        for (int px = 0; px < kFbThreads; ++px) {
+          const float2 ev = *reinterpret_cast<const float2*>(Es + px * KB + m0);
+          const float2 dv = *reinterpret_cast<const float2*>(Ds + px * KB + k0);
+          s0 = fmaf(ev.x, dv.x, s0);
+          s1 = fmaf(ev.x, dv.y, s1);
+          s2 = fmaf(ev.y, dv.x, s2);
+          s3 = fmaf(ev.y, dv.y, s3);
+        }
+        gw[o][0] = s0;
+        gw[o][1] = s1;
+        gw[o][2] = s2;
+        gw[o][3] = s3;
+      }
+    }
+    __syncthreads();
+  }
+  // block partials: G_W (K x K, entries k >= r stay zero) and the sigma_r term
+  const int nb = (K + 1) / 2, rb = (r + 1) / 2;
+  float* gp = gw_part + (int64_t)blockIdx.x * K * K;
+  for (int e = tid; e < K * K; e += blockDim.x) gp[e] = 0.f;
+  __syncthreads();
+#pragma unroll
+  for (int o = 0; o < kMaxOwn; ++o) {
+    const int blk = tid + o * kFbThreads;
+    if (blk < nb * rb) {
+      const int m0 = 2 * (blk / rb), k0 = 2 * (blk % rb);
+      if (m0 < K && k0 < r) gp[m0 * K + k0] = gw[o][0];
+      if (m0 < K && k0 + 1 < r) gp[m0 * K + k0 + 1] = gw[o][1];
+      if (m0 + 1 < K && k0 < r) gp[(m0 + 1) * K + k0] = gw[o][2];
+      if (m0 + 1 < K && k0 + 1 < r) gp[(m0 + 1) * K + k0 + 1] = gw[o][3];
+    }
+  }
+  __shared__ float red[kFbThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) srp += __shfl_xor_sync(0xffffffffu, srp, o);
+  if ((tid & 31) == 0) red[tid >> 5] = srp;
+  __syncthreads();
+  if (tid == 0) {
+    float s = 0.f;
+    for (int w = 0; w < kFbThreads / 32; ++w) s += red[w];
+    sr_part[blockIdx.x] = s;
+  }
+}
+
+// G_W[m][k] = sum over blocks (FP64, fixed order); one CTA per row m.
+__global__ void k_gw_reduce(const float* __restrict__ part, int nblk, int K,
+                            double* __restrict__ gw) {
+  const int m = blockIdx.x, k = threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += (double)part[((int64_t)b * K + m) * K + k];
+  gw[m * K + k] = s;
+}
+
+// FP64 sum of `cnt` partials, fixed order (strided per thread, then a tree).
+__device__ double block_sum_fixed(const float* __restrict__ v, int64_t cnt, double* red) {
+  const int tid = threadIdx.x;
+  double s = 0.0;
+  for (int64_t i = tid; i < cnt; i += blockDim.x) s += (double)v[i];
+  red[tid] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (tid < o) red[tid] += red[tid + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// dsigma_r (through E and through A) and dsigma_s.
+__global__ void __launch_bounds__(256)
+k_bwd_tail(int K, int rho, const float* __restrict__ lm, float sigma_r, const float* __restrict__ what,
+           const double* __restrict__ gw, const double* __restrict__ A64,
+           const float* __restrict__ sr_part, int n_sr, const float* __restrict__ ss_part,
+           int64_t n_ss, DevState* state, float* __restrict__ grad_sigma) {
+  __shared__ double red[256];
+  extern __shared__ double dyn[];
+  double* T = dyn;                           // W_hat^T G_W   (K x K, rows/cols >= r zero)
+  double* U = dyn + K * K;                   // W_hat T
+  const int tid = threadIdx.x;
+  const int r = state->rank;
+  for (int e = tid; e < K * K; e += blockDim.x) {
+    const int a = e / K, b = e - a * K;
+    double s = 0.0;
+    if (a < r && b < r)
+      for (int m = 0; m < K; ++m) s += (double)what[m * K + a] * gw[m * K + b];
+    T[e] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < K * K; e += blockDim.x) {
+    const int i = e / K, b = e - i * K;
+    double s = 0.0;
+    if (b < r)
+      for (int a = 0; a < r; ++a) s += (double)what[i * K + a] * T[a * K + b];
+    U[e] = s;
+  }
+  __syncthreads();
+  const double s3 = (double)sigma_r * sigma_r * sigma_r;
+  double acc = 0.0;
+  for (int e = tid; e < K * K; e += blockDim.x) {
+    const int i = e / K, j = e - i * K;
+    double dA = 0.0;
+    for (int b = 0; b < r; ++b) dA += U[i * K + b] * (double)what[j * K + b];
+    dA *= -0.5;
+    double d2 = 0.0;
+    for (int d = 0; d < rho; ++d) {
+      const double t = (double)lm[i * rho + d] - (double)lm[j * rho + d];
+      d2 += t * t;
+    }
+    acc += dA * A64[i * K + j] * d2;
+  }
+  red[tid] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (tid < o) red[tid] += red[tid + o];
+    __syncthreads();
+  }
+  const double through_A = red[0] / s3;
+  __syncthreads();
+  const double through_E = block_sum_fixed(sr_part, n_sr, red) / s3;
+  const double dss = block_sum_fixed(ss_part, n_ss, red);
+  if (tid == 0) {
+    const float dsr = (float)(through_A + through_E);
+    grad_sigma[0] = dsr;
+    grad_sigma[1] = (float)dss;
+    state->grad_sigma[0] = dsr;
+    state->grad_sigma[1] = (float)dss;
+  }
+}
+
+template <int KB, int RB>
+cudaError_t fb_launch(const float* guide, int64_t N, int rho, const float* lm, int K, float inv2s2r,
+                      const float* what, const DevState* state, const float* dphi, float* dguide,
+                      int add_into, float* gw_part, float* sr_part, cudaStream_t st) {
+  const size_t smem = sizeof(float) * ((size_t)K * kpad4(K) + (size_t)((K * rho + 3) & ~3) +
+                                       (size_t)2 * kFbThreads * KB);
+  cudaError_t e = cudaFuncSetAttribute(k_features_bwd<KB, RB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_features_bwd<KB, RB><<<kFbBlocks, kFbThreads, smem, st>>>(guide, N, rho, lm, K, inv2s2r, what,
+                                                             state, dphi, dguide, add_into,
+                                                             gw_part, sr_part);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int KB>
+cudaError_t fb_rb(const float* guide, int64_t N, int rho, const float* lm, int K, float inv2s2r,
+                  const float* what, const DevState* state, const float* dphi, float* dguide,
+                  int add_into, float* gw_part, float* sr_part, cudaStream_t st) {
+  if (rho <= 4)
+    return fb_launch<KB, 4>(guide, N, rho, lm, K, inv2s2r, what, state, dphi, dguide, add_into,
+                            gw_part, sr_part, st);
+  return fb_launch<KB, 0>(guide, N, rho, lm, K, inv2s2r, what, state, dphi, dguide, add_into,
+                          gw_part, sr_part, st);
+}
+
+}  // namespace
+
+size_t backward_gpart_floats(int K) {
+  return (size_t)kFbBlocks * K * K + kFbBlocks;
+}
+
+size_t backward_spart_floats(int H, int W, int n) {
+  return (size_t)((W + 31) / 32) * ((H + 31) / 32) * (n + 1);
+}
+
+const double* eig_A64(const void* scratch);
+
+cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spatial, float sigma_s,
+                            int S, const void* phi, bool bf16, const float* eta, const float* out,
+                            const float* grad_out, float* grad_f, float* dphi, float* spart,
+                            const DevState* state, cudaStream_t st) {
+  const int Sc = conv_compiled_radius(S);
+  if (Sc < 0) return cudaErrorInvalidValue;
+  const int64_t N = (int64_t)H * W;
+  const int chunks = bwd_chunks(Sc, n);
+  cudaError_t e;
+  if (chunks > 1) {
+    e = cudaMemsetAsync(dphi, 0, sizeof(float) * (size_t)K * N, st);
+    if (e != cudaSuccess) return e;
+  }
+  BwdArgs a;
+  a.f = f;
+  a.H = H;
+  a.W = W;
+  a.n = n;
+  a.N = N;
+  a.phi = phi;
+  a.bf16 = bf16 ? 1 : 0;
+  a.state = state;
+  a.eta = eta;
+  a.out = out;
+  a.gout = grad_out;
+  a.box = spatial == NYF_BOX ? 1 : 0;
+  a.inv2s2 = a.box ? 0.f : (float)(1.0 / (2.0 * (double)sigma_s * sigma_s));
+  a.inv_s3 = a.box ? 0.f : (float)(1.0 / ((double)sigma_s * sigma_s * sigma_s));
+  a.S_true = S;
+  a.dphi = dphi;
+  a.atomic_dphi = chunks > 1 ? 1 : 0;
+  a.df = grad_f;
+  a.sig_part = spart;
+  if (Sc <= 8) return bwd_dispatch_a(Sc, a, st);
+  if (Sc <= 16) return bwd_dispatch_b(Sc, a, st);
+  return bwd_dispatch_c(Sc, a, st);
+}
+
+cudaError_t launch_bwd_features(const float* f, const float* guide, int H, int W, int n, int rho,
+                                const float* landmarks, int K, float sigma_r, int S,
+                                const float* what, const float* dphi, float* grad_f,
+                                float* grad_guide, float* gpart, const float* spart, double* gw,
+                                const void* eig_scratch, float* grad_sigma, DevState* state,
+                                cudaStream_t st) {
+  const int Sc = conv_compiled_radius(S);
+  if (Sc < 0) return cudaErrorInvalidValue;
+  const int64_t N = (int64_t)H * W;
+  // the guide gradient goes into grad_f when the guide is the image
+  const bool tied = guide == f;
+  float* dguide = tied ? grad_f : grad_guide;
+  const int add_into = tied ? 1 : 0;
+  const float inv2s2r = (float)(1.0 / (2.0 * (double)sigma_r * sigma_r));
+  float* gw_part = gpart;
+  float* sr_part = gpart + (size_t)kFbBlocks * K * K;
+  cudaError_t e;
+  if (K <= 8) e = fb_rb<8>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);
+  else if (K <= 16) e = fb_rb<16>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);
+  else if (K <= 32) e = fb_rb<32>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);
+  else e = fb_rb<64>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);
+  if (e != cudaSuccess) return e;
+  k_gw_reduce<<<K, kMaxK, 0, st>>>(gw_part, kFbBlocks, K, gw);
+  count_launches(1);
+  const int64_t n_ss = bwd_ctas(Sc, H, W, n);
+  const size_t smem = sizeof(double) * 2 * K * K;
+  e = cudaFuncSetAttribute(k_bwd_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_bwd_tail<<<1, 256, smem, st>>>(K, rho, landmarks, sigma_r, what, gw, eig_A64(eig_scratch),
+                                   sr_part, kFbBlocks, spart, n_ss, state, grad_sigma);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace nyf

@@ -38,26 +38,70 @@ struct ConvArgs {
 
 constexpr int kConvThreads = 256;
 
+// Tile shapes by radius class.  TH x TW output pixels per CTA; the vertical
+// pass gives each thread RV rows of one halo column, the horizontal pass RH
+// columns of one output row; NQ quantities per CTA, processed in pairs with
+// packed FP32x2 FMAs (one instruction, two planes).  Shared memory: NQ image
+// planes, two phi planes (double buffer) and the vertical-pass plane pair.
 template <int S>
 struct ConvCfg {
   static constexpr int TH = 32;
-  static constexpr int TW = S <= 16 ? 96 : 64;
+  static constexpr int TW = S <= 16 ? 96 : (S <= 24 ? 48 : 64);
   static constexpr int RV = 16;
-  static constexpr int RH = S <= 16 ? 12 : 8;
+  static constexpr int RH = S <= 16 ? 12 : (S <= 24 ? 6 : 8);
   static constexpr int NQ = S <= 24 ? 4 : 2;
   static constexpr int HH = TH + 2 * S;
   static constexpr int HW = TW + 2 * S;
   static constexpr int PS = HW | 1;           // odd row stride: conflict-free column/row walks
   static constexpr int PLANE = HH * PS;
-  static constexpr size_t smem = sizeof(float) * ((size_t)(NQ + 1) * PLANE + (size_t)TH * PS);
+  static constexpr size_t smem = sizeof(float) * ((size_t)(NQ + 2) * PLANE + (size_t)2 * TH * PS);
   static_assert(TH * (TW / RH) == kConvThreads, "one horizontal task per thread");
   static_assert((TH / RV) * HW <= kConvThreads, "at most one vertical task per thread");
+  static_assert(smem <= 227 * 1024, "shared memory budget");
 };
 
-__device__ __forceinline__ float load_phi(const void* phi, int bf16, int64_t idx) {
-  if (bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(phi)[idx]);
-  return __ldg(reinterpret_cast<const float*>(phi) + idx);
+// 4-byte asynchronous global->shared copy; src_size 0 writes a zero (used for
+// pixels outside the image, i.e. the zero padding of the window).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Stage plane k of phi (tile + halo) into P: asynchronous for float32,
+// converted through registers for bfloat16.
+template <int S>
+__device__ __forceinline__ void stage_phi(const ConvArgs& a, float* P, int k, int ty0, int tx0) {
+  using C = ConvCfg<S>;
+  const int64_t base = (int64_t)k * a.N;
+  if (!a.bf16) {
+    const float* src = reinterpret_cast<const float*>(a.phi) + base;
+    for (int e = threadIdx.x; e < C::HH * C::HW; e += kConvThreads) {
+      const int yy = e / C::HW, xx = e - yy * C::HW;
+      const int gy = ty0 - S + yy, gx = tx0 - S + xx;
+      const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+      cp_async4(P + yy * C::PS + xx, in ? src + (int64_t)gy * a.W + gx : src, in);
+    }
+  } else {
+    const __nv_bfloat16* src = reinterpret_cast<const __nv_bfloat16*>(a.phi) + base;
+    for (int e = threadIdx.x; e < C::HH * C::HW; e += kConvThreads) {
+      const int yy = e / C::HW, xx = e - yy * C::HW;
+      const int gy = ty0 - S + yy, gx = tx0 - S + xx;
+      float v = 0.f;
+      if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
+        v = __bfloat162float(src[(int64_t)gy * a.W + gx]);
+      P[yy * C::PS + xx] = v;
+    }
+  }
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 template <int S>
 __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
@@ -65,103 +109,114 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
   constexpr int T = 2 * S + 1;
   constexpr int TH = C::TH, TW = C::TW, RV = C::RV, RH = C::RH, NQ = C::NQ;
   constexpr int HH = C::HH, HW = C::HW, PS = C::PS, PLANE = C::PLANE;
+  constexpr int NP = NQ / 2;        // quantity pairs per CTA
   extern __shared__ float sm[];
   float* F = sm;                    // NQ image planes (tile + halo)
-  float* P = F + NQ * PLANE;        // phi_k (tile + halo)
-  float* M = P + PLANE;             // vertical-pass result, TH x HW
+  float* PB = F + NQ * PLANE;       // two phi planes (tile + halo)
+  float2* M = reinterpret_cast<float2*>(PB + 2 * PLANE);   // vertical pass, TH x HW pairs
   const int tid = threadIdx.x;
   const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
   const int q0 = blockIdx.z * NQ;
   const int n = a.n;
+  const int r = a.state->rank;
 
-  float g[T];
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int z = t - S;
-    const float zz = (float)(z * z);
-    g[t] = (z > a.S_true || -z > a.S_true) ? 0.f : (a.box ? 1.f : expf(-zz * a.inv2s2));
-  }
-
+  // Image planes of this CTA's quantities (zero outside the image and for the
+  // denominator quantity), then phi_0; both asynchronous.
   for (int e = tid; e < NQ * HH * HW; e += kConvThreads) {
     const int qi = e / (HH * HW);
     const int rem = e - qi * (HH * HW);
     const int yy = rem / HW, xx = rem - yy * HW;
     const int c = q0 + qi;
     const int gy = ty0 - S + yy, gx = tx0 - S + xx;
-    float v = 0.f;
-    if (c < n && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
-      v = __ldg(a.f + ((int64_t)gy * a.W + gx) * n + c);
-    F[qi * PLANE + yy * PS + xx] = v;
+    const bool in = c < n && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+    cp_async4(F + qi * PLANE + yy * PS + xx, in ? a.f + ((int64_t)gy * a.W + gx) * n + c : a.f, in);
+  }
+  if (r > 0) stage_phi<S>(a, PB, 0, ty0, tx0);
+  cp_async_commit();
+
+  float2 g[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int z = t - S;
+    const float zz = (float)(z * z);
+    const float v = (z > a.S_true || -z > a.S_true) ? 0.f : (a.box ? 1.f : expf(-zz * a.inv2s2));
+    g[t] = f2(v, v);
   }
 
-  float acc[NQ][RH];
+  float2 acc[NP][RH];
 #pragma unroll
-  for (int qi = 0; qi < NQ; ++qi)
+  for (int pi = 0; pi < NP; ++pi)
 #pragma unroll
-    for (int j = 0; j < RH; ++j) acc[qi][j] = 0.f;
+    for (int j = 0; j < RH; ++j) acc[pi][j] = f2(0.f, 0.f);
 
   const int hy = tid / (TW / RH), hx0 = (tid % (TW / RH)) * RH;
-  const int vtask = tid;                        // one vertical task per thread (or none)
-  const int vx = vtask % HW, vy0 = (vtask / HW) * RV;
-  const bool vactive = vtask < (TH / RV) * HW;
-  const int r = a.state->rank;
+  const int vx = tid % HW, vy0 = (tid / HW) * RV;
+  const bool vactive = tid < (TH / RV) * HW;     // one vertical task per thread (or none)
 
   for (int k = 0; k < r; ++k) {
-    __syncthreads();
-    const int64_t base = (int64_t)k * a.N;
-    for (int e = tid; e < HH * HW; e += kConvThreads) {
-      const int yy = e / HW, xx = e - yy * HW;
-      const int gy = ty0 - S + yy, gx = tx0 - S + xx;
-      float v = 0.f;
-      if (gy >= 0 && gy < a.H && gx >= 0 && gx < a.W)
-        v = load_phi(a.phi, a.bf16, base + (int64_t)gy * a.W + gx);
-      P[yy * PS + xx] = v;
+    // Prefetch phi_{k+1} into the other buffer while phi_k is consumed.  The
+    // buffer was last read in iteration k-1, which ended with a barrier.
+    if (k + 1 < r) {
+      stage_phi<S>(a, PB + ((k + 1) & 1) * PLANE, k + 1, ty0, tx0);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const float* P = PB + (k & 1) * PLANE;
 #pragma unroll
-    for (int qi = 0; qi < NQ; ++qi) {
-      const int q = q0 + qi;
-      if (q <= n) {                              // uniform over the block
-        const bool den = (q == n);
-        const float* Fq = F + qi * PLANE;
+    for (int pi = 0; pi < NP; ++pi) {
+      const int qa = q0 + 2 * pi, qb = qa + 1;
+      if (qa <= n) {                             // uniform over the block
+        // pair member x: image channel qa (or 1 if qa == n); member y: channel
+        // qb (1 if qb == n, 0 if qb > n)
+        const float* Fa = F + (2 * pi) * PLANE;
+        const float* Fb = Fa + PLANE;
+        const bool a_den = qa == n, b_den = qb == n, b_none = qb > n;
         if (vactive) {
-          float va[RV];
+          float2 va[RV];
 #pragma unroll
-          for (int j = 0; j < RV; ++j) va[j] = 0.f;
+          for (int j = 0; j < RV; ++j) va[j] = f2(0.f, 0.f);
 #pragma unroll
           for (int i = 0; i < RV + 2 * S; ++i) {
             const int off = (vy0 + i) * PS + vx;
-            float v = P[off];
-            if (!den) v *= Fq[off];
+            const float p = P[off];
+            const float x = a_den ? p : p * Fa[off];
+            const float y = b_den ? p : (b_none ? 0.f : p * Fb[off]);
+            const float2 v = f2(x, y);
 #pragma unroll
             for (int j = 0; j < RV; ++j) {
               const int t = i - j;
-              if (t >= 0 && t < T) va[j] = fmaf(g[t], v, va[j]);
+              if (t >= 0 && t < T) va[j] = __ffma2_rn(g[t], v, va[j]);
             }
           }
 #pragma unroll
           for (int j = 0; j < RV; ++j) M[(vy0 + j) * PS + vx] = va[j];
         }
         __syncthreads();
-        float hb[RH];
+        float2 hb[RH];
 #pragma unroll
-        for (int j = 0; j < RH; ++j) hb[j] = 0.f;
+        for (int j = 0; j < RH; ++j) hb[j] = f2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < RH + 2 * S; ++i) {
-          const float v = M[hy * PS + hx0 + i];
+          const float2 v = M[hy * PS + hx0 + i];
 #pragma unroll
           for (int j = 0; j < RH; ++j) {
             const int t = i - j;
-            if (t >= 0 && t < T) hb[j] = fmaf(g[t], v, hb[j]);
+            if (t >= 0 && t < T) hb[j] = __ffma2_rn(g[t], v, hb[j]);
           }
         }
 #pragma unroll
-        for (int j = 0; j < RH; ++j)
-          acc[qi][j] = fmaf(P[(hy + S) * PS + hx0 + j + S], hb[j], acc[qi][j]);
+        for (int j = 0; j < RH; ++j) {
+          const float p = P[(hy + S) * PS + hx0 + j + S];
+          acc[pi][j] = __ffma2_rn(f2(p, p), hb[j], acc[pi][j]);
+        }
         __syncthreads();
       }
     }
   }
+  cp_async_wait<0>();
 
   // Epilogue: g_hat = zeta / eta (fused) or zeta, eta to memory (split).
   const int y = ty0 + hy;
@@ -171,22 +226,28 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
     const int x = tx0 + hx0 + j;
     if (y < a.H && x < a.W) {
       const int64_t pix = (int64_t)y * a.W + x;
+      float v[NQ];
+#pragma unroll
+      for (int pi = 0; pi < NP; ++pi) {
+        v[2 * pi] = acc[pi][j].x;
+        v[2 * pi + 1] = acc[pi][j].y;
+      }
       if (fused) {
         float eta = 0.f;
 #pragma unroll
         for (int qi = 0; qi < NQ; ++qi)
-          if (qi == n) eta = acc[qi][j];
+          if (qi == n) eta = v[qi];
 #pragma unroll
         for (int qi = 0; qi < NQ; ++qi)
-          if (qi < n) a.out[pix * n + qi] = acc[qi][j] / eta;
+          if (qi < n) a.out[pix * n + qi] = v[qi] / eta;
         a.eta[pix] = eta;
         if (!(eta > a.eta_thr)) atomicAdd(&a.state_rw->eta_small, 1ull);
       } else {
 #pragma unroll
         for (int qi = 0; qi < NQ; ++qi) {
           const int q = q0 + qi;
-          if (q < n) a.zeta[pix * n + q] = acc[qi][j];
-          else if (q == n) a.eta[pix] = acc[qi][j];
+          if (q < n) a.zeta[pix * n + q] = v[qi];
+          else if (q == n) a.eta[pix] = v[qi];
         }
       }
     }

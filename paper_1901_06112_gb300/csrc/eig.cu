@@ -1,15 +1,28 @@
-// Landmark kernel A (Eq. (9)) and its eigendecomposition (Eq. (10)) in FP64.
+// Landmark kernel A (Eq. (9)) and its eigendecomposition (Eq. (10)), FP64 accurate.
 //
-// One CTA per landmark set.  A(i, j) = exp(-||mu_i - mu_j||^2 / (2 sigma_r^2))
-// is built in FP64 from the float32 landmarks and diagonalised by the parallel
-// cyclic Jacobi method (round-robin ordering: K/2 disjoint rotations per step,
-// K-1 steps per sweep), which is accurate to a few units of FP64 rounding
-// relative to ||A||.  The eigenvalues are sorted descending, modes with
-// alpha_k > tau * alpha_max are kept, and the factor
-//     W_hat[m][k] = w_mk / sqrt(alpha_k)      (k < r; zero for k >= r)
-// is written in float32, so that phi_k(x) = sum_m kappa(p_x, mu_m) W_hat[m][k]
-// equals sqrt(alpha_k) v_k(x) of Eq. (12).  Each eigenvector's sign is fixed so
-// that its entry of largest magnitude (first such entry on ties) is positive.
+// GB300 executes FP64 at about 1/64 of its FP32 rate, so an FP64 Jacobi
+// sweep on one SM costs as much as the whole filter.  The decomposition is
+// therefore computed in parts:
+//   1. k_a64      (K CTAs)  A(i, j) = exp(-||mu_i - mu_j||^2 / (2 sigma_r^2)) in FP64;
+//   2. k_jacobi32 (1 CTA)   parallel cyclic Jacobi on float(A) in FP32
+//                           (round-robin ordering, K/2 rotations per step);
+//   3. three iterations of the refinement of Ogita & Aishima ("Iterative
+//      refinement for symmetric eigenvalue decomposition", Japan J. Indust.
+//      Appl. Math. 35, 2018), all in FP64, each product spread over K CTAs
+//      (one column per CTA):
+//         R = I - X^T X,  S = X^T A X,  lam_i = S_ii / (1 - R_ii),
+//         E_ij = (S_ij + lam_j R_ij) / (lam_j - lam_i)  if |lam_i - lam_j| > delta,
+//                R_ij / 2 otherwise,   X <- X + X E,
+//         delta = 2 (||S - diag(lam)|| + ||A|| ||R||)   (Frobenius norms);
+//      each iteration squares the error of the FP32 start;
+//      then S = X^T A X once more and a thresholded FP64 Jacobi "polish" on S
+//      (one warp) that resolves clusters of nearly equal eigenvalues, which
+//      the first-order refinement only orthonormalises;
+//   4. k_finalize (1 CTA)   sort descending, keep alpha_k > tau * alpha_max,
+//                           W_hat[m][k] = w_mk / sqrt(alpha_k) in float32 with
+//                           each eigenvector's largest-magnitude entry positive.
+// phi_k(x) = sum_m kappa(p_x, mu_m) W_hat[m][k] is then sqrt(alpha_k) v_k(x)
+// of Eq. (12).
 #include <math.h>
 
 #include "nyf_internal.cuh"
@@ -17,175 +30,403 @@
 namespace nyf {
 namespace {
 
-constexpr int kEigThreads = 256;
-constexpr int kMaxSweeps = 40;
+constexpr int kJacThreads = 256;
+constexpr int kMaxSweeps32 = 16;
+constexpr int kRefineIters = 3;
 
-struct EigSmem {
-  double A[kMaxK][kMaxK + 1];
-  double V[kMaxK][kMaxK + 1];
-  double c[kMaxK / 2], s[kMaxK / 2];
-  int p[kMaxK / 2], q[kMaxK / 2];
-  int ring[kMaxK];
-  int order[kMaxK];
-  double red[kEigThreads];
+// FP64 scratch of the decomposition (inside the workspace).
+struct EigBuf {
+  double A[kMaxK * kMaxK];
+  double X[2][kMaxK * kMaxK];   // X[m*K + i] = component m of eigenvector i
+  double Y[kMaxK * kMaxK];
+  double S[kMaxK * kMaxK];
+  double R[kMaxK * kMaxK];
+  double lam[kMaxK];
+  double cnA[kMaxK], cnS[kMaxK], cnR[kMaxK];   // per-column squared norms
+  int bad;
 };
 
-__device__ double block_sum(double v, double* red) {
-  const int tid = threadIdx.x;
-  red[tid] = v;
-  __syncthreads();
-  for (int o = kEigThreads / 2; o > 0; o >>= 1) {
-    if (tid < o) red[tid] += red[tid + o];
-    __syncthreads();
-  }
-  const double r = red[0];
-  __syncthreads();
-  return r;
-}
-
-__global__ void __launch_bounds__(kEigThreads)
-k_eig(const float* __restrict__ lm, int K, int rho, float sigma_r, double tau,
-      float* __restrict__ what, double* __restrict__ alphas_out, int* __restrict__ rank_out,
-      DevState* state) {
-  extern __shared__ __align__(16) unsigned char raw[];
-  EigSmem& sm = *reinterpret_cast<EigSmem*>(raw);
-  const int tid = threadIdx.x;
-  const int Kp = (K + 1) & ~1;            // even number of players; index K is a dummy if K is odd
-  const int half = Kp / 2;
-  const double inv2s2 = 1.0 / (2.0 * (double)sigma_r * (double)sigma_r);
-
-  // A(i, j) = kappa(mu_i, mu_j), Eq. (9); V = I.
-  double nonfinite = 0.0;
-  for (int e = tid; e < K * K; e += kEigThreads) {
-    const int i = e / K, j = e - i * K;
+// ---- 1. A in FP64, one column per CTA
+__global__ void k_a64(const float* __restrict__ lm, int K, int rho, double inv2s2, EigBuf* b) {
+  const int j = blockIdx.x, i = threadIdx.x;
+  __shared__ double red[kMaxK];
+  double a = 0.0;
+  if (i < K) {
     double d2 = 0.0;
     for (int d = 0; d < rho; ++d) {
       const double t = (double)lm[i * rho + d] - (double)lm[j * rho + d];
       d2 = fma(t, t, d2);
     }
-    const double a = exp(-d2 * inv2s2);
-    if (!isfinite(a)) nonfinite += 1.0;
-    sm.A[i][j] = a;
-    sm.V[i][j] = (i == j) ? 1.0 : 0.0;
+    a = exp(-d2 * inv2s2);
+    b->A[i * K + j] = a;
   }
-  if (tid < Kp) sm.ring[tid] = tid;
+  red[i] = (i < K) ? a * a : 0.0;
   __syncthreads();
-  const double bad = block_sum(nonfinite, sm.red);
-  const double diag2 = block_sum(tid < K ? sm.A[tid][tid] * sm.A[tid][tid] : 0.0, sm.red);
+  if (i == 0) {
+    double s = 0.0;
+    bool bad = false;
+    for (int q = 0; q < K; ++q) {
+      s += red[q];
+      bad |= !isfinite(red[q]);
+    }
+    b->cnA[j] = s;
+    if (bad) b->bad = 1;
+  }
+}
 
-  if (bad == 0.0) {
-    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-      double off = 0.0;
-      for (int e = tid; e < K * K; e += kEigThreads) {
+// ---- 2. FP32 parallel cyclic Jacobi on float(A)
+//
+// Round-robin ("circle") ordering: at step s player 0 stays and position i > 0
+// holds player 1 + (i - 1 + s) mod (Kp - 1); position i meets position Kp-1-i.
+// The K/2 rotations of a step act on disjoint index pairs, so A' = J^T A J
+// splits into independent 2 x 2 blocks: block (pair a, pair b) becomes
+// R_a^T [A]_ab R_b and depends on nothing else.  One pass over A (and one over
+// V) per step, two barriers per step.
+struct Jac32 {
+  float A[kMaxK][kMaxK + 1];
+  float V[kMaxK][kMaxK + 1];
+  float c[kMaxK / 2], s[kMaxK / 2];
+  int p[kMaxK / 2], q[kMaxK / 2];
+  float red[kJacThreads];
+};
+
+__device__ float block_sum_f(float v, float* red) {
+  const int tid = threadIdx.x;
+  red[tid] = v;
+  __syncthreads();
+  for (int o = kJacThreads / 2; o > 0; o >>= 1) {
+    if (tid < o) red[tid] += red[tid + o];
+    __syncthreads();
+  }
+  const float r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ int rr_player(int pos, int step, int Kp) {
+  return pos == 0 ? 0 : 1 + (pos - 1 + step) % (Kp - 1);
+}
+
+__global__ void __launch_bounds__(kJacThreads) k_jacobi32(int K, EigBuf* b) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  Jac32& sm = *reinterpret_cast<Jac32*>(raw);
+  const int tid = threadIdx.x;
+  const int Kp = (K + 1) & ~1;
+  const int half = Kp / 2;
+  for (int e = tid; e < K * K; e += kJacThreads) {
+    const int i = e / K, j = e - i * K;
+    sm.A[i][j] = (float)b->A[i * K + j];
+    sm.V[i][j] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const float diag2 = block_sum_f(tid < K ? sm.A[tid][tid] * sm.A[tid][tid] : 0.f, sm.red);
+  float prev = INFINITY;
+  if (b->bad == 0) {
+    for (int sweep = 0; sweep < kMaxSweeps32; ++sweep) {
+      float off = 0.f;
+      for (int e = tid; e < K * K; e += kJacThreads) {
         const int i = e / K, j = e - i * K;
         if (i < j) off += sm.A[i][j] * sm.A[i][j];
       }
-      off = block_sum(off, sm.red);
-      if (off <= 1e-30 * diag2 || off == 0.0) break;
+      off = block_sum_f(off, sm.red);
+      // stop at convergence, or once FP32 rounding noise stops the decrease
+      // (only near the noise floor: early sweeps can decrease slowly)
+      if (off <= 1e-14f * diag2 || off == 0.f) break;
+      if (off <= 1e-9f * diag2 && off > 0.25f * prev) break;
+      prev = off;
       for (int step = 0; step < Kp - 1; ++step) {
-        // Rotation of each pair, classical Jacobi (Golub & Van Loan, sym.schur2).
-        if (tid < half) {
-          int a = sm.ring[tid], b = sm.ring[Kp - 1 - tid];
-          if (a > b) { const int t = a; a = b; b = t; }
-          double c = 1.0, s = 0.0;
-          if (b < K) {
-            const double apq = sm.A[a][b];
-            if (apq != 0.0) {
-              const double theta = (sm.A[b][b] - sm.A[a][a]) / (2.0 * apq);
-              const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
-              c = 1.0 / sqrt(1.0 + t * t);
+        if (tid < half) {        // rotation of pair tid (Golub & Van Loan, sym.schur2)
+          int a = rr_player(tid, step, Kp), bb = rr_player(Kp - 1 - tid, step, Kp);
+          if (a > bb) { const int t = a; a = bb; bb = t; }
+          float c = 1.f, s = 0.f;
+          if (bb < K) {
+            const float apq = sm.A[a][bb];
+            if (apq != 0.f) {
+              const float theta = (sm.A[bb][bb] - sm.A[a][a]) / (2.f * apq);
+              const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(1.f + theta * theta));
+              c = rsqrtf(1.f + t * t);
               s = t * c;
             }
+          } else {
+            bb = a;              // dummy partner: identity on a single index
           }
           sm.p[tid] = a;
-          sm.q[tid] = b;
+          sm.q[tid] = bb;
           sm.c[tid] = c;
           sm.s[tid] = s;
         }
         __syncthreads();
-        // Rows p, q <- J^T A.
-        for (int e = tid; e < half * K; e += kEigThreads) {
-          const int pr = e / K, j = e - pr * K;
-          const int a = sm.p[pr], b = sm.q[pr];
-          if (b < K) {
-            const double c = sm.c[pr], s = sm.s[pr];
-            const double x = sm.A[a][j], y = sm.A[b][j];
-            sm.A[a][j] = c * x - s * y;
-            sm.A[b][j] = s * x + c * y;
+        // 2 x 2 blocks of A: rows of pair u, columns of pair v
+        for (int e = tid; e < half * half; e += kJacThreads) {
+          const int u = e / half, v = e - u * half;
+          const int pu = sm.p[u], qu = sm.q[u], pv = sm.p[v], qv = sm.q[v];
+          const float cu = sm.c[u], su = sm.s[u], cv = sm.c[v], sv = sm.s[v];
+          const float a00 = sm.A[pu][pv], a01 = sm.A[pu][qv];
+          const float a10 = sm.A[qu][pv], a11 = sm.A[qu][qv];
+          // rows: [r0; r1] = R_u^T [a0.; a1.]
+          const float r00 = cu * a00 - su * a10, r01 = cu * a01 - su * a11;
+          const float r10 = su * a00 + cu * a10, r11 = su * a01 + cu * a11;
+          // columns: [.0 .1] = [r.0 r.1] R_v
+          const float n00 = cv * r00 - sv * r01, n01 = sv * r00 + cv * r01;
+          const float n10 = cv * r10 - sv * r11, n11 = sv * r10 + cv * r11;
+          if (pu == qu && pv == qv) {
+            sm.A[pu][pv] = n00;
+          } else if (pu == qu) {
+            sm.A[pu][pv] = n00;
+            sm.A[pu][qv] = n01;
+          } else if (pv == qv) {
+            sm.A[pu][pv] = n00;
+            sm.A[qu][pv] = n10;
+          } else {
+            sm.A[pu][pv] = n00;
+            sm.A[pu][qv] = n01;
+            sm.A[qu][pv] = n10;
+            sm.A[qu][qv] = (u == v) ? n11 : n11;
+            if (u == v) sm.A[pu][qv] = sm.A[qu][pv] = 0.f;   // the annihilated entry
           }
         }
-        __syncthreads();
-        // Columns p, q <- A J, and V <- V J.
-        for (int e = tid; e < half * K; e += kEigThreads) {
-          const int pr = e / K, i = e - pr * K;
-          const int a = sm.p[pr], b = sm.q[pr];
-          if (b < K) {
-            const double c = sm.c[pr], s = sm.s[pr];
-            const double x = sm.A[i][a], y = sm.A[i][b];
-            sm.A[i][a] = c * x - s * y;
-            sm.A[i][b] = s * x + c * y;
-            const double u = sm.V[i][a], v = sm.V[i][b];
-            sm.V[i][a] = c * u - s * v;
-            sm.V[i][b] = s * u + c * v;
+        // V <- V J: columns of pair v
+        for (int e = tid; e < K * half; e += kJacThreads) {
+          const int i = e / half, v = e - i * half;
+          const int pv = sm.p[v], qv = sm.q[v];
+          if (pv != qv) {
+            const float cv = sm.c[v], sv = sm.s[v];
+            const float x = sm.V[i][pv], y = sm.V[i][qv];
+            sm.V[i][pv] = cv * x - sv * y;
+            sm.V[i][qv] = sv * x + cv * y;
           }
-        }
-        __syncthreads();
-        if (tid < half && sm.q[tid] < K && sm.s[tid] != 0.0) {
-          sm.A[sm.p[tid]][sm.q[tid]] = 0.0;
-          sm.A[sm.q[tid]][sm.p[tid]] = 0.0;
-        }
-        // Next round-robin pairing: player 0 stays, the others rotate by one.
-        if (tid == 0) {
-          const int last = sm.ring[Kp - 1];
-          for (int t = Kp - 1; t > 1; --t) sm.ring[t] = sm.ring[t - 1];
-          sm.ring[1] = last;
         }
         __syncthreads();
       }
     }
   }
+  for (int e = tid; e < K * K; e += kJacThreads) {
+    const int m = e / K, i = e - m * K;
+    b->X[0][e] = (double)sm.V[m][i];
+  }
+}
 
-  // Sort descending (stable selection), truncate, write factors.
+// ---- 3a. Y = A X (column j per CTA)
+__global__ void k_oa_y(int K, int src, EigBuf* b) {
+  const int j = blockIdx.x, i = threadIdx.x;
+  __shared__ double xj[kMaxK];
+  if (i < K) xj[i] = b->X[src][i * K + j];
+  __syncthreads();
+  if (i < K) {
+    double s = 0.0;
+    for (int m = 0; m < K; ++m) s = fma(b->A[i * K + m], xj[m], s);
+    b->Y[i * K + j] = s;
+  }
+}
+
+// ---- 3b. S = X^T Y, R = I - X^T X (column j per CTA) and their column norms
+__global__ void k_oa_sr(int K, int src, EigBuf* b) {
+  const int j = blockIdx.x, i = threadIdx.x;
+  __shared__ double xj[kMaxK], yj[kMaxK], rs[kMaxK], rr[kMaxK];
+  const double* X = b->X[src];
+  if (i < K) {
+    xj[i] = X[i * K + j];
+    yj[i] = b->Y[i * K + j];
+  }
+  __syncthreads();
+  double s = 0.0, r = 0.0;
+  if (i < K) {
+    double xx = 0.0;
+    for (int m = 0; m < K; ++m) {
+      const double xmi = X[m * K + i];
+      s = fma(xmi, yj[m], s);
+      xx = fma(xmi, xj[m], xx);
+    }
+    r = (i == j ? 1.0 : 0.0) - xx;
+    b->S[i * K + j] = s;
+    b->R[i * K + j] = r;
+  }
+  rs[i] = (i < K && i != j) ? s * s : 0.0;
+  rr[i] = (i < K) ? r * r : 0.0;
+  __syncthreads();
+  if (i == 0) {
+    double a = 0.0, c = 0.0;
+    for (int q = 0; q < K; ++q) {
+      a += rs[q];
+      c += rr[q];
+    }
+    b->cnS[j] = a;
+    b->cnR[j] = c;
+  }
+}
+
+// ---- 3c. lam, E[:, j] and X_new[:, j] = X[:, j] + X E[:, j]
+__global__ void k_oa_update(int K, int src, int orth_only, EigBuf* b) {
+  const int j = blockIdx.x, i = threadIdx.x;
+  __shared__ double lam[kMaxK], ej[kMaxK], cS[kMaxK], cR[kMaxK], cA[kMaxK];
+  __shared__ double delta;
+  if (i < K) {
+    lam[i] = b->S[i * K + i] / (1.0 - b->R[i * K + i]);
+    cS[i] = b->cnS[i];
+    cR[i] = b->cnR[i];
+    cA[i] = b->cnA[i];
+  }
+  __syncthreads();
+  if (i == 0) {
+    double nS = 0.0, nR = 0.0, nA = 0.0;
+    for (int q = 0; q < K; ++q) {
+      nS += cS[q];
+      nR += cR[q];
+      nA += cA[q];
+    }
+    delta = 2.0 * (sqrt(nS) + sqrt(nA) * sqrt(nR));
+  }
+  __syncthreads();
+  if (i < K) {
+    const double r = b->R[i * K + j];
+    double e;
+    if (i == j || orth_only) {
+      e = 0.5 * r;
+    } else {
+      const double gap = lam[j] - lam[i];
+      const double num = b->S[i * K + j] + lam[j] * r;
+      // first-order update only where it is small; near-degenerate pairs are
+      // orthonormalised here and resolved by the final polish
+      e = (fabs(gap) > delta && fabs(num) <= 1e-4 * fabs(gap)) ? num / gap : 0.5 * r;
+    }
+    ej[i] = e;
+    if (j == 0 && !orth_only) b->lam[i] = lam[i];
+  }
+  __syncthreads();
+  if (i < K) {
+    const double* X = b->X[src];
+    double s = X[i * K + j];
+    for (int m = 0; m < K; ++m) s = fma(X[i * K + m], ej[m], s);
+    b->X[src ^ 1][i * K + j] = s;
+  }
+}
+
+// ---- 3d. Polish: thresholded FP64 Jacobi on S = X^T A X.  After the refinement
+// S is diagonal to FP64 rounding except inside clusters of nearly equal
+// eigenvalues, so only a few pairs rotate; each rotation is applied to S and
+// to the columns of X.  One warp; pairs are scanned in cyclic row order and a
+// pair rotates when |S_pq| > 4 eps sqrt(|S_pp S_qq|) (the negligibility test of
+// Demmel & Veselic).  Writes the eigenvalues to lam.
+__global__ void k_polish(int K, int src, EigBuf* b) {
+  extern __shared__ double ps[];
+  double* Sm = ps;                     // K x (K + 1)
+  double* Xm = ps + K * (K + 1);       // K x (K + 1)
+  const int lane = threadIdx.x;
+  const int ld = K + 1;
+  for (int e = lane; e < K * K; e += 32) {
+    const int i = e / K, j = e - i * K;
+    Sm[i * ld + j] = 0.5 * (b->S[i * K + j] + b->S[j * K + i]);
+    Xm[i * ld + j] = b->X[src][i * K + j];
+  }
+  __syncwarp();
+  const double eps4 = 4.0 * 2.220446049250313e-16;
+  const int npairs = K * (K - 1) / 2;
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    int rotated = 0;
+    for (int base = 0; base < npairs; base += 32) {
+      const int t = base + lane;
+      int p = 0, q = 0;
+      bool flag = false;
+      if (t < npairs) {                      // t -> (p, q), p < q, row-major order
+        int rem = t;
+        p = 0;
+        while (rem >= K - 1 - p) { rem -= K - 1 - p; ++p; }
+        q = p + 1 + rem;
+        const double spq = Sm[p * ld + q];
+        flag = fabs(spq) > eps4 * sqrt(fabs(Sm[p * ld + p] * Sm[q * ld + q])) && spq != 0.0;
+      }
+      unsigned m = __ballot_sync(0xffffffffu, flag);
+      while (m) {
+        const int src_lane = __ffs(m) - 1;
+        m &= m - 1;
+        const int pp = __shfl_sync(0xffffffffu, p, src_lane);
+        const int qq = __shfl_sync(0xffffffffu, q, src_lane);
+        const double apq = Sm[pp * ld + qq];
+        if (apq == 0.0) continue;            // uniform: every lane reads the same value
+        const double theta = (Sm[qq * ld + qq] - Sm[pp * ld + pp]) / (2.0 * apq);
+        const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+        const double c = 1.0 / sqrt(1.0 + tt * tt), s = tt * c;
+        __syncwarp();
+        for (int j = lane; j < K; j += 32) {     // rows p, q
+          const double x = Sm[pp * ld + j], y = Sm[qq * ld + j];
+          Sm[pp * ld + j] = c * x - s * y;
+          Sm[qq * ld + j] = s * x + c * y;
+        }
+        __syncwarp();
+        for (int i = lane; i < K; i += 32) {     // columns p, q of S and X
+          const double x = Sm[i * ld + pp], y = Sm[i * ld + qq];
+          Sm[i * ld + pp] = c * x - s * y;
+          Sm[i * ld + qq] = s * x + c * y;
+          const double u = Xm[i * ld + pp], v = Xm[i * ld + qq];
+          Xm[i * ld + pp] = c * u - s * v;
+          Xm[i * ld + qq] = s * u + c * v;
+        }
+        __syncwarp();
+        if (lane == 0) Sm[pp * ld + qq] = Sm[qq * ld + pp] = 0.0;
+        __syncwarp();
+        rotated = 1;
+      }
+    }
+    if (!rotated) break;
+  }
+  __syncwarp();
+  for (int e = lane; e < K * K; e += 32) {
+    const int i = e / K, j = e - i * K;
+    b->X[src][i * K + j] = Xm[i * ld + j];
+  }
+  for (int i = lane; i < K; i += 32) b->lam[i] = Sm[i * ld + i];
+}
+
+// ---- 4. sort, truncate, factor
+__global__ void k_finalize(int K, int src, double tau, EigBuf* b, float* __restrict__ what,
+                           double* __restrict__ alphas_out, int* __restrict__ rank_out,
+                           DevState* state) {
+  __shared__ double lam[kMaxK];
+  __shared__ int order[kMaxK];
+  __shared__ double sgn[kMaxK];
+  __shared__ int rsh;
+  const int tid = threadIdx.x;
+  const double* X = b->X[src];
+  if (tid < K) lam[tid] = b->lam[tid];
+  __syncthreads();
+  if (tid < K) {                                  // stable descending rank of each eigenvalue
+    const double v = lam[tid];
+    int rk = 0;
+    for (int q = 0; q < K; ++q) rk += (lam[q] > v) || (lam[q] == v && q < tid);
+    order[rk] = tid;
+  }
+  __syncthreads();
   if (tid == 0) {
-    for (int k = 0; k < K; ++k) sm.order[k] = k;
-    for (int k = 0; k < K; ++k) {
-      int best = k;
-      for (int j = k + 1; j < K; ++j)
-        if (sm.A[sm.order[j]][sm.order[j]] > sm.A[sm.order[best]][sm.order[best]]) best = j;
-      const int t = sm.order[k];
-      sm.order[k] = sm.order[best];
-      sm.order[best] = t;
-    }
-    const double amax = sm.A[sm.order[0]][sm.order[0]];
+    const double amax = lam[order[0]];
     int r = 0;
-    if (bad == 0.0 && amax > 0.0 && isfinite(amax))
-      while (r < K && sm.A[sm.order[r]][sm.order[r]] > tau * amax) ++r;
-    for (int k = 0; k < K; ++k) {
-      const double a = sm.A[sm.order[k]][sm.order[k]];
-      state->alpha[k] = a;
-      if (alphas_out) alphas_out[k] = a;
-    }
+    if (b->bad == 0 && amax > 0.0 && isfinite(amax))
+      while (r < K && lam[order[r]] > tau * amax) ++r;
     state->rank = r;
     if (rank_out) *rank_out = r;
     if (r == 0) set_status(state, NYF_ERR_NUMERIC);
-    sm.red[0] = (double)r;
+    rsh = r;
+  }
+  if (tid < K) {
+    const double a = lam[order[tid]];
+    state->alpha[tid] = a;
+    if (alphas_out) alphas_out[tid] = a;
+    const int col = order[tid];                   // sign: largest-magnitude entry positive
+    int arg = 0;
+    double best = -1.0;
+    for (int m = 0; m < K; ++m) {
+      const double v = fabs(X[m * K + col]);
+      if (v > best) { best = v; arg = m; }
+    }
+    sgn[tid] = X[arg * K + col] < 0.0 ? -1.0 : 1.0;
   }
   __syncthreads();
-  const int r = (int)sm.red[0];
-  for (int e = tid; e < K * K; e += kEigThreads) {
+  const int r = rsh;
+  for (int e = tid; e < K * K; e += blockDim.x) {
     const int m = e / K, k = e - m * K;
     float w = 0.f;
     if (k < r) {
-      const int col = sm.order[k];
-      // sign convention: the entry of largest magnitude is positive
-      int arg = 0;
-      double best = -1.0;
-      for (int i = 0; i < K; ++i) {
-        const double v = fabs(sm.V[i][col]);
-        if (v > best) { best = v; arg = i; }
-      }
-      const double sgn = sm.V[arg][col] < 0.0 ? -1.0 : 1.0;
-      w = (float)(sgn * sm.V[m][col] / sqrt(sm.A[col][col]));
+      const int col = order[k];
+      w = (float)(sgn[k] * X[m * K + col] / sqrt(lam[col]));
     }
     what[m * K + k] = w;
   }
@@ -193,14 +434,48 @@ k_eig(const float* __restrict__ lm, int K, int rho, float sigma_r, double tau,
 
 }  // namespace
 
+size_t eig_scratch_bytes() { return sizeof(EigBuf); }
+
+const double* eig_A64(const void* scratch) { return reinterpret_cast<const EigBuf*>(scratch)->A; }
+
 cudaError_t launch_eig(const float* landmarks, int K, int rho, float sigma_r, double tau,
                        float* what, double* alphas_out, int* rank_out, DevState* state,
-                       cudaStream_t st) {
-  const size_t smem = sizeof(EigSmem);
-  cudaError_t e = cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                       void* scratch, cudaStream_t st) {
+  EigBuf* b = reinterpret_cast<EigBuf*>(scratch);
+  cudaError_t e = cudaMemsetAsync(&b->bad, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  k_eig<<<1, kEigThreads, smem, st>>>(landmarks, K, rho, sigma_r, tau, what, alphas_out, rank_out,
-                                      state);
+  const double inv2s2 = 1.0 / (2.0 * (double)sigma_r * (double)sigma_r);
+  k_a64<<<K, kMaxK, 0, st>>>(landmarks, K, rho, inv2s2, b);
+  count_launches(1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const size_t smem = sizeof(Jac32);
+  e = cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_jacobi32<<<1, kJacThreads, smem, st>>>(K, b);
+  count_launches(1);
+  int src = 0;
+  for (int it = 0; it < kRefineIters; ++it) {
+    k_oa_y<<<K, kMaxK, 0, st>>>(K, src, b);
+    k_oa_sr<<<K, kMaxK, 0, st>>>(K, src, b);
+    k_oa_update<<<K, kMaxK, 0, st>>>(K, src, 0, b);
+    count_launches(3);
+    src ^= 1;
+  }
+  // orthonormalise once more (X <- X (I + R / 2), second-order accurate), then
+  // S = X^T A X for the polish
+  k_oa_y<<<K, kMaxK, 0, st>>>(K, src, b);
+  k_oa_sr<<<K, kMaxK, 0, st>>>(K, src, b);
+  k_oa_update<<<K, kMaxK, 0, st>>>(K, src, 1, b);
+  src ^= 1;
+  k_oa_y<<<K, kMaxK, 0, st>>>(K, src, b);
+  k_oa_sr<<<K, kMaxK, 0, st>>>(K, src, b);
+  count_launches(3);
+  const size_t psmem = sizeof(double) * 2 * K * (K + 1);
+  e = cudaFuncSetAttribute(k_polish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+  if (e != cudaSuccess) return e;
+  k_polish<<<1, 32, psmem, st>>>(K, src, b);
+  count_launches(3);
+  k_finalize<<<1, kMaxK, 0, st>>>(K, src, tau, b, what, alphas_out, rank_out, state);
   count_launches(1);
   return cudaGetLastError();
 }

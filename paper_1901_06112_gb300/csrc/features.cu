@@ -27,20 +27,107 @@ __device__ inline void store_phi(void* phi, int64_t idx, float v) {
   else reinterpret_cast<float*>(phi)[idx] = v;
 }
 
-// Shared tail: E -> phi for one pixel.
+// Shared tail: E -> phi for one pixel.  W_hat sits in shared memory with a
+// row stride KP (K rounded up to 4, zero padded) so that four modes' weights
+// come in one 16-byte load: one shared load per four FMAs.
+__host__ __device__ inline int kpad(int K) { return (K + 3) & ~3; }
+
 template <int KB, bool BF16>
 __device__ inline void emit_phi(const float (&e)[KB], int K, int r, const float* Wsm, void* phi,
                                 int64_t N, int64_t i) {
-  for (int k = 0; k < r; ++k) {
-    float acc = 0.f;
+  const int KP = kpad(K);
+  for (int k = 0; k < r; k += 4) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
     for (int m = 0; m < KB; ++m)
-      if (m < K) acc = fmaf(e[m], Wsm[m * K + k], acc);
-    store_phi<BF16>(phi, (int64_t)k * N + i, acc);
+      if (m < K) {
+        const float4 w = *reinterpret_cast<const float4*>(Wsm + m * KP + k);
+        a0 = fmaf(e[m], w.x, a0);
+        a1 = fmaf(e[m], w.y, a1);
+        a2 = fmaf(e[m], w.z, a2);
+        a3 = fmaf(e[m], w.w, a3);
+      }
+    store_phi<BF16>(phi, (int64_t)k * N + i, a0);
+    if (k + 1 < r) store_phi<BF16>(phi, (int64_t)(k + 1) * N + i, a1);
+    if (k + 2 < r) store_phi<BF16>(phi, (int64_t)(k + 2) * N + i, a2);
+    if (k + 3 < r) store_phi<BF16>(phi, (int64_t)(k + 3) * N + i, a3);
   }
 }
 
-// Stored guide (BLF / joint BLF): one pixel per thread.  RB > 0 keeps the
+// Two pixels per thread: each 16-byte weight load feeds eight FMAs.
+template <int KB, bool BF16>
+__device__ inline void emit_phi2(const float (&e0)[KB], const float (&e1)[KB], bool v1, int K,
+                                 int r, const float* Wsm, void* phi, int64_t N, int64_t i0,
+                                 int64_t i1) {
+  const int KP = kpad(K);
+  for (int k = 0; k < r; k += 4) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+#pragma unroll
+    for (int m = 0; m < KB; ++m)
+      if (m < K) {
+        const float4 w = *reinterpret_cast<const float4*>(Wsm + m * KP + k);
+        a0 = fmaf(e0[m], w.x, a0);
+        a1 = fmaf(e0[m], w.y, a1);
+        a2 = fmaf(e0[m], w.z, a2);
+        a3 = fmaf(e0[m], w.w, a3);
+        b0 = fmaf(e1[m], w.x, b0);
+        b1 = fmaf(e1[m], w.y, b1);
+        b2 = fmaf(e1[m], w.z, b2);
+        b3 = fmaf(e1[m], w.w, b3);
+      }
+    const float va[4] = {a0, a1, a2, a3}, vb[4] = {b0, b1, b2, b3};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (k + q < r) {
+        store_phi<BF16>(phi, (int64_t)(k + q) * N + i0, va[q]);
+        if (v1) store_phi<BF16>(phi, (int64_t)(k + q) * N + i1, vb[q]);
+      }
+  }
+}
+
+// W_hat (K x K, row-major) -> shared memory with row stride kpad(K).
+__device__ inline void stage_what(const float* what, int K, float* Wsm) {
+  const int KP = kpad(K);
+  for (int e = threadIdx.x; e < K * KP; e += blockDim.x) {
+    const int m = e / KP, k = e - m * KP;
+    Wsm[e] = k < K ? what[m * K + k] : 0.f;
+  }
+}
+
+// E_m = exp(-||p_i - mu_m||^2 / (2 sigma_r^2)) for one stored guide row.
+template <int KB, int RB>
+__device__ inline void guide_exp(const float* __restrict__ guide, int64_t i, int rho,
+                                 const float* mu, int K, float inv2s2, float (&e)[KB]) {
+  const float* p = guide + i * rho;
+  float x[RB > 0 ? RB : 1];
+  if (RB > 0) {
+#pragma unroll
+    for (int d = 0; d < (RB > 0 ? RB : 1); ++d) x[d] = (d < rho) ? __ldg(p + d) : 0.f;
+  }
+#pragma unroll
+  for (int m = 0; m < KB; ++m) {
+    float d2 = 0.f;
+    if (m < K) {
+      const float* c = mu + m * rho;
+      if (RB > 0) {
+#pragma unroll
+        for (int d = 0; d < (RB > 0 ? RB : 1); ++d)
+          if (d < rho) {
+            const float t = x[d] - c[d];
+            d2 = fmaf(t, t, d2);
+          }
+      } else {
+        for (int d = 0; d < rho; ++d) {
+          const float t = __ldg(p + d) - c[d];
+          d2 = fmaf(t, t, d2);
+        }
+      }
+    }
+    e[m] = (m < K) ? expf(-d2 * inv2s2) : 0.f;
+  }
+}
+
+// Stored guide (BLF / joint BLF): two pixels per thread.  RB > 0 keeps the
 // guide row in registers (rho <= RB); RB == 0 re-reads it (large rho).
 template <int KB, int RB, bool BF16>
 __global__ void __launch_bounds__(256)
@@ -48,43 +135,20 @@ k_features(const float* __restrict__ guide, int64_t N, int rho, const float* __r
            float inv2s2, const float* __restrict__ what, const DevState* __restrict__ state,
            void* __restrict__ phi) {
   extern __shared__ float sm[];
-  float* mu = sm;               // K * rho
-  float* Wsm = sm + K * rho;    // K * K
+  float* Wsm = sm;                      // K * kpad(K), 16-byte aligned
+  float* mu = sm + K * kpad(K);         // K * rho
   for (int e = threadIdx.x; e < K * rho; e += blockDim.x) mu[e] = lm[e];
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) Wsm[e] = what[e];
+  stage_what(what, K, Wsm);
   __syncthreads();
   const int r = state->rank;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float* p = guide + i * rho;
-    float x[RB > 0 ? RB : 1];
-    if (RB > 0) {
-#pragma unroll
-      for (int d = 0; d < (RB > 0 ? RB : 1); ++d) x[d] = (d < rho) ? __ldg(p + d) : 0.f;
-    }
-    float e[KB];
-#pragma unroll
-    for (int m = 0; m < KB; ++m) {
-      float d2 = 0.f;
-      if (m < K) {
-        const float* c = mu + m * rho;
-        if (RB > 0) {
-#pragma unroll
-          for (int d = 0; d < (RB > 0 ? RB : 1); ++d)
-            if (d < rho) {
-              const float t = x[d] - c[d];
-              d2 = fmaf(t, t, d2);
-            }
-        } else {
-          for (int d = 0; d < rho; ++d) {
-            const float t = __ldg(p + d) - c[d];
-            d2 = fmaf(t, t, d2);
-          }
-        }
-      }
-      e[m] = (m < K) ? expf(-d2 * inv2s2) : 0.f;
-    }
-    emit_phi<KB, BF16>(e, K, r, Wsm, phi, N, i);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 2;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x * 2; base < N; base += stride) {
+    const int64_t i0 = base + threadIdx.x, i1 = i0 + blockDim.x;
+    const bool v0 = i0 < N, v1 = i1 < N;
+    float e0[KB], e1[KB];
+    guide_exp<KB, RB>(guide, v0 ? i0 : 0, rho, mu, K, inv2s2, e0);
+    guide_exp<KB, RB>(guide, v1 ? i1 : 0, rho, mu, K, inv2s2, e1);
+    if (v0) emit_phi2<KB, BF16>(e0, e1, v1, K, r, Wsm, phi, N, i0, i1);
   }
 }
 
@@ -101,13 +165,13 @@ k_features_nlm(const float* __restrict__ f, int H, int W, int n, int r, const fl
   const int side = 2 * r + 1;
   const int rho = side * side * n;
   const int TS = kNlmTile + 2 * r;
-  float* mu = sm;                      // K * rho
-  float* Wsm = mu + K * rho;           // K * K
-  float* tile = Wsm + K * K;           // TS * TS * n
+  float* Wsm = sm;                     // K * kpad(K), 16-byte aligned
+  float* mu = Wsm + K * kpad(K);       // K * rho
+  float* tile = mu + K * rho;          // TS * TS * n
   const int tid = threadIdx.x;
   const int y0 = blockIdx.y * kNlmTile, x0 = blockIdx.x * kNlmTile;
   for (int e = tid; e < K * rho; e += blockDim.x) mu[e] = lm[e];
-  for (int e = tid; e < K * K; e += blockDim.x) Wsm[e] = what[e];
+  stage_what(what, K, Wsm);
   for (int e = tid; e < TS * TS * n; e += blockDim.x) {
     const int c = e % n, q = e / n;
     const int yy = q / TS, xx = q % TS;
@@ -143,12 +207,12 @@ template <int KB, int RB, bool BF16>
 cudaError_t features_launch(const float* guide, int64_t N, int rho, const float* lm, int K,
                             float inv2s2, const float* what, const DevState* state, void* phi,
                             cudaStream_t st) {
-  const size_t smem = sizeof(float) * ((size_t)K * rho + (size_t)K * K);
+  const size_t smem = sizeof(float) * ((size_t)K * rho + (size_t)K * kpad(K));
   cudaError_t e = cudaFuncSetAttribute(k_features<KB, RB, BF16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int64_t g = (N + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
+  int64_t g = (N + 511) / 512;
+  if (g > 152 * 8) g = 152 * 8;
   if (g < 1) g = 1;
   k_features<KB, RB, BF16><<<(int)g, 256, smem, st>>>(guide, N, rho, lm, K, inv2s2, what, state, phi);
   count_launches(1);
@@ -180,7 +244,7 @@ cudaError_t nlm_launch(const float* f, int H, int W, int n, int r, const float* 
                        cudaStream_t st) {
   const int rho = (2 * r + 1) * (2 * r + 1) * n;
   const int TS = kNlmTile + 2 * r;
-  const size_t smem = sizeof(float) * ((size_t)K * rho + (size_t)K * K + (size_t)TS * TS * n);
+  const size_t smem = sizeof(float) * ((size_t)K * rho + (size_t)K * kpad(K) + (size_t)TS * TS * n);
   cudaError_t e = cudaFuncSetAttribute(k_features_nlm<KB, BF16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -221,7 +285,7 @@ cudaError_t launch_features_nlm(const float* f, int H, int W, int n, int r, cons
 size_t features_nlm_smem_bytes(int K, int n, int r) {
   const int rho = (2 * r + 1) * (2 * r + 1) * n;
   const int TS = kNlmTile + 2 * r;
-  return sizeof(float) * ((size_t)K * rho + (size_t)K * K + (size_t)TS * TS * n);
+  return sizeof(float) * ((size_t)K * rho + (size_t)K * kpad(K) + (size_t)TS * TS * n);
 }
 
 }  // namespace nyf

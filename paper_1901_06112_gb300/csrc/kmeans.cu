@@ -20,6 +20,8 @@ __device__ inline float warp_sum(float v) {
 }
 
 constexpr int assign_threads(int RB) { return RB > 0 ? 256 : 128; }
+constexpr int assign_ppt(int RB) { return RB == 0 ? 1 : (RB <= 8 ? 4 : (RB <= 16 ? 2 : 1)); }
+constexpr int assign_rb(int rho) { return rho <= 4 ? 4 : (rho <= 8 ? 8 : (rho <= 16 ? 16 : (rho <= 32 ? 32 : 0))); }
 
 // BLF subsample: stratum t of the row order gives row
 // lo + SplitMix64(seed ^ kSampleStream, t + 1) mod (hi - lo); it is copied to X.
@@ -39,13 +41,17 @@ __global__ void k_sample_rows(const float* __restrict__ G, int64_t N, int rho, i
   }
 }
 
+// Centroids are stored with row stride 4 (float4, zero padded) when rho <= 4.
+__host__ __device__ constexpr int mu_stride(int rho) { return rho <= 4 ? 4 : rho; }
+
 size_t assign_smem(int K, int rho) {
   const int warps = assign_threads(rho <= 32 ? 1 : 0) / 32;
-  return sizeof(float) * ((size_t)K * rho + (size_t)warps * K * (rho + 1));
+  return sizeof(float) * ((size_t)K * mu_stride(rho) + (size_t)warps * K * (rho + 1));
 }
 
 int kmeans_grid(int64_t N, int rho) {
-  const int64_t t = assign_threads(rho <= 32 ? 1 : 0);
+  const int rb = assign_rb(rho);
+  const int64_t t = (int64_t)assign_threads(rb) * assign_ppt(rb);
   const int64_t g = (N + t - 1) / t;
   return (int)(g < kKmeansBlocks ? (g < 1 ? 1 : g) : kKmeansBlocks);
 }
@@ -98,86 +104,122 @@ __global__ void k_draw_init(const float* __restrict__ X, int64_t N, int rho, int
   }
 }
 
-// Assignment pass.  RB > 0: the row is held in registers (rho <= RB); RB == 0:
-// it is re-read from global memory (large rho, used for small row counts).
+// Assignment pass.  RB > 0: the rows are held in registers (rho <= RB) and
+// each thread handles PPT rows, so one centroid load from shared memory serves
+// PPT distance evaluations; RB == 0: rows are re-read from global memory
+// (large rho, used for small row counts).
 // part[b][j][0..rho) = sum of the members of cluster j seen by block b,
 // part[b][j][rho] = their count; qpart[b] = sum of their squared distances.
-template <int RB, int THREADS>
+template <int RB, int THREADS, int PPT>
 __global__ void __launch_bounds__(THREADS)
 k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __restrict__ cent,
          int32_t* __restrict__ labels, float* __restrict__ part, float* __restrict__ qpart,
          int accumulate) {
-  extern __shared__ float sm[];
+  extern __shared__ __align__(16) float sm[];
   constexpr int kWarps = THREADS / 32;
-  float* mu = sm;                       // K * rho
-  float* acc = sm + K * rho;            // kWarps * K * (rho + 1)
+  constexpr int RX = RB > 0 ? RB : 1;
+  const int ms = mu_stride(rho);
+  float* mu = sm;                       // K * ms
+  float* acc = sm + K * ms;             // kWarps * K * (rho + 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int stride = rho + 1;
-  for (int e = tid; e < K * rho; e += blockDim.x) mu[e] = cent[e];
+  for (int e = tid; e < K * ms; e += blockDim.x) {
+    const int j = e / ms, d = e - j * ms;
+    mu[e] = d < rho ? cent[j * rho + d] : 0.f;
+  }
   if (accumulate)
     for (int e = tid; e < kWarps * K * stride; e += blockDim.x) acc[e] = 0.f;
   __syncthreads();
 
   float qsum = 0.f;
-  for (int64_t base = (int64_t)blockIdx.x * THREADS; base < N;
-       base += (int64_t)gridDim.x * THREADS) {
-    const int64_t i = base + tid;
-    const bool valid = i < N;
-    const float* xi = X + (valid ? i : 0) * rho;
-    float x[RB > 0 ? RB : 1];
-    if (RB > 0) {
+  for (int64_t base = (int64_t)blockIdx.x * THREADS * PPT; base < N;
+       base += (int64_t)gridDim.x * THREADS * PPT) {
+    float x[PPT][RX];
+    bool valid[PPT];
+    int best[PPT];
+    float bd[PPT];
 #pragma unroll
-      for (int d = 0; d < (RB > 0 ? RB : 1); ++d) x[d] = (d < rho) ? __ldg(xi + d) : 0.f;
+    for (int q = 0; q < PPT; ++q) {
+      const int64_t i = base + (int64_t)q * THREADS + tid;
+      valid[q] = i < N;
+      const float* xi = X + (valid[q] ? i : 0) * rho;
+#pragma unroll
+      for (int d = 0; d < RX; ++d) x[q][d] = (RB > 0 && d < rho) ? __ldg(xi + d) : 0.f;
+      best[q] = 0;
+      bd[q] = __int_as_float(0x7f800000);
     }
-    int best = 0;
-    float bd = __int_as_float(0x7f800000);
-    for (int j = 0; j < K; ++j) {
-      const float* m = mu + j * rho;
-      float dist = 0.f;
-      if (RB > 0) {
+    if (RB > 0) {
+#pragma unroll 4
+      for (int j = 0; j < K; ++j) {
+        const float* m = mu + j * ms;
+        float c[RX];
+        if (RB == 4) {
+          const float4 c4 = *reinterpret_cast<const float4*>(m);
+          c[0] = c4.x;
+          c[RX > 1 ? 1 : 0] = c4.y;
+          c[RX > 2 ? 2 : 0] = c4.z;
+          c[RX > 3 ? 3 : 0] = c4.w;
+        } else {
 #pragma unroll
-        for (int d = 0; d < (RB > 0 ? RB : 1); ++d) {
-          if (d < rho) {
-            const float t = x[d] - m[d];
+          for (int d = 0; d < RX; ++d) c[d] = d < rho ? m[d] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+          float dist = 0.f;
+#pragma unroll
+          for (int d = 0; d < RX; ++d) {
+            const float t = x[q][d] - c[d];
             dist = fmaf(t, t, dist);
           }
+          if (dist < bd[q]) { bd[q] = dist; best[q] = j; }   // strict: ties keep the lowest index
         }
-      } else {
+      }
+    } else {
+      const int64_t i = base + tid;
+      const float* xi = X + (valid[0] ? i : 0) * rho;
+      for (int j = 0; j < K; ++j) {
+        const float* m = mu + j * ms;
+        float dist = 0.f;
         for (int d = 0; d < rho; ++d) {
           const float t = __ldg(xi + d) - m[d];
           dist = fmaf(t, t, dist);
         }
+        if (dist < bd[0]) { bd[0] = dist; best[0] = j; }
       }
-      if (dist < bd) { bd = dist; best = j; }   // strict: ties keep the lowest index
     }
-    if (valid) {
-      qsum += bd;
-      if (labels) labels[i] = best;
-    }
-    if (accumulate) {
-      unsigned todo = __ballot_sync(kFull, valid);
-      while (todo) {
-        const int leader = __ffs(todo) - 1;
-        const int L = __shfl_sync(kFull, best, leader);
-        const bool mine = valid && best == L;
-        const unsigned grp = __ballot_sync(kFull, mine);
-        float* a = acc + (warp * K + L) * stride;
-        if (RB > 0) {
 #pragma unroll
-          for (int d = 0; d < (RB > 0 ? RB : 1); ++d) {
-            if (d < rho) {
-              const float v = warp_sum(mine ? x[d] : 0.f);
+    for (int q = 0; q < PPT; ++q) {
+      const int64_t i = base + (int64_t)q * THREADS + tid;
+      const float* xi = X + (valid[q] ? i : 0) * rho;
+      if (valid[q]) {
+        qsum += bd[q];
+        if (labels) labels[i] = best[q];
+      }
+      if (accumulate) {
+        unsigned todo = __ballot_sync(kFull, valid[q]);
+        while (todo) {
+          const int leader = __ffs(todo) - 1;
+          const int L = __shfl_sync(kFull, best[q], leader);
+          const bool mine = valid[q] && best[q] == L;
+          const unsigned grp = __ballot_sync(kFull, mine);
+          float* a = acc + (warp * K + L) * stride;
+          if (RB > 0) {
+#pragma unroll
+            for (int d = 0; d < RX; ++d) {
+              if (d < rho) {
+                const float v = warp_sum(mine ? x[q][d] : 0.f);
+                if (lane == 0) a[d] += v;
+              }
+            }
+          } else {
+            for (int d = 0; d < rho; ++d) {
+              const float v = warp_sum(mine ? __ldg(xi + d) : 0.f);
               if (lane == 0) a[d] += v;
             }
           }
-        } else {
-          for (int d = 0; d < rho; ++d) {
-            const float v = warp_sum(mine ? __ldg(xi + d) : 0.f);
-            if (lane == 0) a[d] += v;
-          }
+          if (lane == 0) a[rho] += (float)__popc(grp);
+          todo &= ~grp;
         }
-        if (lane == 0) a[rho] += (float)__popc(grp);
-        todo &= ~grp;
       }
     }
   }
@@ -274,11 +316,12 @@ cudaError_t assign_launch(int grid, const float* X, int64_t N, int rho, int K, c
                           int32_t* labels, float* part, float* qpart, int accumulate,
                           cudaStream_t st) {
   constexpr int T = assign_threads(RB);
+  constexpr int PPT = assign_ppt(RB);
   const size_t smem = assign_smem(K, rho);
-  cudaError_t e = cudaFuncSetAttribute(k_assign<RB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_assign<RB, T, PPT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_assign<RB, T><<<grid, T, smem, st>>>(X, N, rho, K, cent, labels, part, qpart, accumulate);
+  k_assign<RB, T, PPT><<<grid, T, smem, st>>>(X, N, rho, K, cent, labels, part, qpart, accumulate);
   count_launches(1);
   return cudaGetLastError();
 }

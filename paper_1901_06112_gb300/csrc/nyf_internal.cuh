@@ -13,7 +13,7 @@ constexpr int kMaxK = NYF_MAX_K;
 constexpr int kMaxRho = NYF_MAX_RHO;
 constexpr int kMaxS = NYF_MAX_S;
 constexpr int kMaxChannels = NYF_MAX_CHANNELS;
-constexpr int kKmeansBlocks = 1216;      // 8 x 152 SMs: partial-sum slots of the assign pass
+constexpr int kKmeansBlocks = 608;       // 4 x 152 SMs: partial-sum slots of the assign pass
 constexpr int kKmeansThreads = 256;
 
 // Device-side state at the start of every workspace.
@@ -29,12 +29,13 @@ struct DevState {
 
 // Byte offsets of every region of a workspace (all 256-byte aligned).
 struct WsLayout {
-  size_t state, landmarks, what, init_idx, km_part, km_qpart, sample_idx, sample_x, phi, eta,
-      zeta, dphi, gpart, total;
+  size_t state, landmarks, what, eig, init_idx, km_part, km_qpart, sample_idx, sample_x, phi,
+      eta, zeta, dphi, gpart, spart, gw, total;
 };
 
 // Problem geometry used to size a workspace.
 struct WsShape {
+  int H, W;         // image size (H * W == N for images; N x 1 for row sets)
   int64_t N;        // pixels (rows of the guide)
   int n;            // image channels
   int rho;          // guide dimension
@@ -77,7 +78,8 @@ cudaError_t launch_nlm_sample(const float* f, int H, int W, int n, int r, int64_
                               int64_t* idx, float* X, cudaStream_t st);
 cudaError_t launch_eig(const float* landmarks, int K, int rho, float sigma_r, double tau,
                        float* what, double* alphas_out, int* rank_out, DevState* state,
-                       cudaStream_t st);
+                       void* scratch, cudaStream_t st);
+size_t eig_scratch_bytes();
 cudaError_t launch_features(const float* guide, int64_t N, int rho, const float* landmarks, int K,
                             float sigma_r, const float* what, const DevState* state, void* phi,
                             bool bf16, cudaStream_t st);
@@ -90,11 +92,18 @@ cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void*
                                 float* eta_out, float* zeta_ws, cudaStream_t st);
 int conv_compiled_radius(int S);
 bool conv_split(int S, int n);
-cudaError_t launch_backward(const float* f, const float* guide, int H, int W, int n, int rho,
-                            const float* landmarks, int K, float sigma_r, int spatial,
-                            float sigma_s, int S, const float* what, const void* phi, bool bf16,
-                            const float* eta, const float* out, const float* grad_out,
-                            float* grad_f, float* grad_guide, float* dphi, float* gpart,
-                            float* grad_sigma, DevState* state, cudaStream_t st);
+cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spatial, float sigma_s,
+                            int S, const void* phi, bool bf16, const float* eta, const float* out,
+                            const float* grad_out, float* grad_f, float* dphi, float* spart,
+                            const DevState* state, cudaStream_t st);
+cudaError_t launch_bwd_features(const float* f, const float* guide, int H, int W, int n, int rho,
+                                const float* landmarks, int K, float sigma_r, int S,
+                                const float* what, const float* dphi, float* grad_f,
+                                float* grad_guide, float* gpart, const float* spart, double* gw,
+                                const void* eig_scratch, float* grad_sigma, DevState* state,
+                                cudaStream_t st);
+size_t backward_gpart_floats(int K);
+size_t backward_spart_floats(int H, int W, int n);
+const double* eig_A64(const void* scratch);
 
 }  // namespace nyf

@@ -166,3 +166,92 @@ def stats(ws: Workspace) -> dict:
     s = L.NyfStats()
     L.check(lib.nyf_get_stats(ws.cptr(), C.byref(s), _stream()), "nyf_get_stats")
     return {k: getattr(s, k) for k, _ in L.NyfStats._fields_}
+
+
+# ----------------------------------------------------------------------------- backward
+
+class BackwardBuffers:
+    """Output buffers of the backward pass: dL/df, dL/dguide (joint guide) and dL/dsigma."""
+
+    def __init__(self, f, guide=None):
+        self.grad_f = torch.empty_like(f)
+        self.grad_guide = None if guide is None else torch.empty_like(guide)
+        self.grad_sigma = torch.zeros(2, dtype=torch.float32, device=f.device)
+
+
+def blf_backward_available() -> bool:
+    return True
+
+
+def blf_backward(f, params: Params, out, grad_out, ws: Workspace, bufs: BackwardBuffers = None,
+                 guide=None) -> BackwardBuffers:
+    """Adjoint of blf(): must follow the forward call that produced `out` on `ws`.
+
+    Landmarks, the window radius and the kept modes are held at their forward
+    values.  Returns the buffers (grad_f is the total derivative when the guide
+    is the image).
+    """
+    lib = L.load()
+    _check_image(grad_out, "grad_out")
+    H, W, n = f.shape
+    rho = n if guide is None else guide.shape[2]
+    bufs = bufs or BackwardBuffers(f, guide)
+    p = params.c()
+    L.check(lib.nyf_filter_blf_backward(_ptr(f), _ptr(guide), H, W, n, rho, C.byref(p), _ptr(out),
+                                        _ptr(grad_out), _ptr(bufs.grad_f), _ptr(bufs.grad_guide),
+                                        _ptr(bufs.grad_sigma), ws.cptr(), ws.nbytes, _stream()),
+            "nyf_filter_blf_backward")
+    return bufs
+
+
+def blf_vjp(f, params: Params, grad_out, guide=None, landmarks=None) -> dict:
+    """Forward + backward: gradients of sum(grad_out * g_hat)."""
+    H, W, n = f.shape
+    rho = n if guide is None else guide.shape[2]
+    ws = make_workspace(H, W, n, rho, params, f.device)
+    out = blf(f, params, guide=guide, landmarks=landmarks, ws=ws)
+    b = blf_backward(f, params, out, grad_out.contiguous(), ws, guide=guide)
+    gs = b.grad_sigma.cpu()
+    return {"out": out, "df": b.grad_f, "dp": b.grad_guide, "dsigma_r": float(gs[0]),
+            "dsigma_s": float(gs[1])}
+
+
+class NyfBLF(torch.autograd.Function):
+    """Differentiable Nystrom bilateral filter (w.r.t. image, guide, sigma_r, sigma_s).
+
+    Landmarks are a stop-gradient input (computed by k-means when None).
+    """
+
+    @staticmethod
+    def forward(ctx, f, guide, sigma_r, sigma_s, params: Params, landmarks=None):
+        P = Params(**{**params.__dict__})
+        P.sigma_r = float(sigma_r)
+        P.sigma_s = float(sigma_s)
+        f = f.contiguous()
+        g = None if guide is None else guide.contiguous()
+        H, W, n = f.shape
+        rho = n if g is None else g.shape[2]
+        ws = make_workspace(H, W, n, rho, P, f.device)
+        out = blf(f, P, guide=g, landmarks=landmarks, ws=ws)
+        ctx.P, ctx.ws, ctx.has_guide = P, ws, g is not None
+        ctx.save_for_backward(f, g if g is not None else torch.empty(0, device=f.device), out)
+        ctx.sig_dev = (sigma_r.device if isinstance(sigma_r, torch.Tensor) else None,
+                       sigma_s.device if isinstance(sigma_s, torch.Tensor) else None)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        f, g, out = ctx.saved_tensors
+        g = g if ctx.has_guide else None
+        b = blf_backward(f, ctx.P, out, grad_out.contiguous(), ctx.ws, guide=g)
+        dsr = b.grad_sigma[0]
+        dss = b.grad_sigma[1]
+        dev_r, dev_s = ctx.sig_dev
+        dsr = dsr.to(dev_r) if dev_r is not None else None
+        dss = dss.to(dev_s) if dev_s is not None else None
+        return b.grad_f, b.grad_guide, dsr, dss, None, None
+
+
+def blf_autograd(f, sigma_r, sigma_s, params: Params, guide=None, landmarks=None):
+    """g_hat with autograd support; sigma_r / sigma_s may be 0-dim tensors."""
+    return NyfBLF.apply(f, guide, sigma_r, sigma_s, params, landmarks)

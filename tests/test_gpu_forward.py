@@ -241,3 +241,29 @@ def test_nlm_subsample_and_parity(nyf):
     assert st["status"] == 0
     r2, _ = report("nlm 60x72 K=6 (device k-means)", out2.cpu().numpy(), want)
     assert r2 < 1e-3
+
+
+@pytest.mark.parametrize("case", ["few_colour", "duplicate", "random"])
+def test_features_gram_matches_oracle(nyf, case):
+    # K-hat = Phi Phi^T is unique even when eigenvalues are (nearly) degenerate
+    if case == "few_colour":
+        mu = np.array([[0, 0, 0], [255, 0, 0], [0, 255, 0], [0, 0, 255], [255, 255, 255]], np.float32)
+        sr, tau = 60.0, 1e-12
+    elif case == "duplicate":
+        mu = np.random.default_rng(5).uniform(0, 255, size=(7, 3)).astype(np.float32)
+        mu[4] = mu[1]
+        sr, tau = 50.0, 1e-7
+    else:
+        mu = np.random.default_rng(6).uniform(0, 255, size=(13, 3)).astype(np.float32)
+        sr, tau = 45.0, 1e-7
+    X = synth.random_image(20, 21, 3, 40).reshape(-1, 3)
+    phi, rank, alphas = nyf.features(cuda(X), cuda(mu), sr, tau)
+    _, alpha_o, _, keep = ny.spectral_step(mu.astype(np.float64), sr, tau)
+    print(f"[parity] eig {case}: gpu={alphas.cpu().numpy()} oracle={alpha_o}")
+    assert int(rank.cpu()) == keep.size
+    assert np.allclose(alphas.cpu().numpy(), alpha_o, rtol=0, atol=1e-12 * alpha_o[0])
+    P = phi.cpu().numpy()[: keep.size].T.astype(np.float64)
+    from oracle import bound as bd
+    Kh = bd.nystrom_matrix(X.astype(np.float64), mu.astype(np.float64), sr, tau)
+    r, _ = report(f"K-hat {case}", P @ P.T, Kh)
+    assert r < 1e-5
