@@ -122,6 +122,26 @@ nyf_status nyf_features(const float* guide, int64_t N, int rho, const float* lan
                         float sigma_r, double eig_rel_tol, int precision, void* phi, int* rank,
                         double* alphas, void* ws, size_t ws_bytes, void* stream);
 
+/* nyf_features for callers that cannot allocate device memory (a plain C host
+ * without a device allocator, a plugin whose host owns all device memory, a
+ * latency-critical loop where cudaMalloc would synchronise the device).  The
+ * paper has no counterpart: this is a deployment variant of nyf_features.
+ * Same arguments and results as nyf_features, without ws/ws_bytes: its scratch
+ * (status word, W_hat factor, FP64 eigendecomposition buffers) is a fixed
+ * 256 KiB array in device memory that every GPU loading the library holds
+ * until the process exits.  The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress, with the device current) and caches it; make
+ * that first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents, so calls that overlap on the GPU race.
+ * Returns NYF_ERR_UNSUPPORTED for K > NYF_STATIC_MAX_K or
+ * rho > NYF_STATIC_MAX_RHO, NYF_ERR_CUDA if the address lookup fails.
+ * Allocates nothing. */
+#define NYF_STATIC_MAX_K 64
+#define NYF_STATIC_MAX_RHO 160
+nyf_status nyf_features_static(const float* guide, int64_t N, int rho, const float* landmarks,
+                               int K, float sigma_r, double eig_rel_tol, int precision, void* phi,
+                               int* rank, double* alphas, void* stream);
+
 /* Nystrom bilateral filter, Algorithm 1 with output Eqs. (14)-(15).
  *   f          H x W x n image (device)
  *   guide      H x W x rho guide (joint BLF), or NULL: guide = f (rho must equal n)

@@ -59,6 +59,8 @@ _SIGNATURES = {
     "nyf_set_timing": (None, [C.c_int]),
     "nyf_get_timing": (C.c_int, [C.POINTER(C.c_float), C.c_int]),
     "nyf_launch_count": (C.c_longlong, []),
+    "nyf_features_static": (C.c_int, [_P, C.c_int64, C.c_int, _P, C.c_int, C.c_float, C.c_double,
+                                      C.c_int, _P, _P, _P, _P]),
 }
 OPTIONAL = {
     "nyf_batched_workspace_size": (C.c_size_t, [_P, C.c_int, C.c_int, C.c_int, C.c_int]),
