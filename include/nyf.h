@@ -108,16 +108,18 @@ nyf_status nyf_kmeans(const float* X, int64_t N, int rho, int K, int iters, uint
                       void* ws, size_t ws_bytes, void* stream);
 
 /* Nystrom per-pixel features (Eqs. (9)-(12)).  For landmarks mu (K x rho):
- * A(i,j) = kappa(mu_i, mu_j) is decomposed in FP64 (Eq. (10)), and for every
- * row p_x of `guide` (N x rho) and kept mode k
- *     phi_k(x) = sum_m kappa(p_x, mu_m) w_mk / sqrt(alpha_k)
- * = sqrt(alpha_k) v_k(x) of Eq. (12), so that K-hat = sum_k phi_k phi_k^T.
- *   phi     output, K planes of N values (plane k at phi + k * N), float32
- *           (NYF_FP32) or bfloat16 (NYF_BF16); planes k >= r are left unchanged
- *   rank    1 int output (device) or NULL
- *   alphas  K doubles output (device): all eigenvalues of A, descending, or NULL
- * Eigenvector signs are not fixed by Eq. (10); phi is unique up to the sign
- * of each plane (and rotations within equal eigenvalues). */
+ * A(i,j) = kappa(mu_i, mu_j) is decomposed to FP64 accuracy (Eq. (10)),
+ * modes with alpha_k > eig_rel_tol * alpha_max are kept (r of them), and for
+ * every row p_x of `guide` (N x rho)
+ *     phi_j(x) = sum_m kappa(p_x, mu_m) W[m][j],   j < K,
+ * with the symmetric factor W = W_r Lambda_r^{-1/2} W_r^T (= A_r^{-1/2}), so
+ * that sum_j phi_j(x) phi_j(y) = K-hat(x, y) = sum_{k<r} alpha_k v_k(x) v_k(y)
+ * with v_k of Eq. (12).  The symmetric factor is unique (no eigenvector sign
+ * or rotation freedom) and keeps the features well conditioned.
+ *   phi     output, K planes of N values (plane j at phi + j * N), float32
+ *           (NYF_FP32) or bfloat16 (NYF_BF16)
+ *   rank    1 int output (device): r, or NULL
+ *   alphas  K doubles output (device): all eigenvalues of A, descending, or NULL */
 nyf_status nyf_features(const float* guide, int64_t N, int rho, const float* landmarks, int K,
                         float sigma_r, double eig_rel_tol, int precision, void* phi, int* rank,
                         double* alphas, void* ws, size_t ws_bytes, void* stream);

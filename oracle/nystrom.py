@@ -201,3 +201,19 @@ def features(p: np.ndarray, mu: np.ndarray, sigma_r: float, tau: float):
     phi = np.stack([np.sqrt(alpha[k]) * extrapolate(B, Wv[:, k], alpha[k]) for k in keep], axis=1) \
         if keep.size else np.zeros((R.shape[0], 0))
     return phi, alpha, keep
+
+
+def features_symmetric(p: np.ndarray, mu: np.ndarray, sigma_r: float, tau: float):
+    """Features for the symmetric factor of the truncated inverse of A.
+
+    phi_j(x) = sum_m B(m, x) W[m, j] with W = W_r Lambda_r^{-1/2} W_r^T, so that
+    Phi Phi^T = B^T W_r Lambda_r^{-1} W_r^T B = sum_k alpha_k v_k v_k^T = K-hat
+    (Eq. (8) with Eq. (12)).  Unlike ``features`` this factor is unique.
+    Returns (phi: N x m0, alpha, keep).
+    """
+    p = np.asarray(p, np.float64)
+    R = p.reshape(-1, p.shape[-1])
+    _, alpha, Wv, keep = spectral_step(mu, sigma_r, tau)
+    Wr = Wv[:, keep]
+    Wsym = (Wr / np.sqrt(alpha[keep])) @ Wr.T
+    return cross_kernel(mu, R, sigma_r).T @ Wsym, alpha, keep

@@ -39,7 +39,7 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
   float* Es = mu + ((K * rho + 3) & ~3);    // kFbThreads x KB
   float* Ds = Es + kFbThreads * KB;         // kFbThreads x KB
   const int tid = threadIdx.x;
-  const int r = state->rank;
+  const int r = state->planes;
   for (int e = tid; e < K * KP; e += blockDim.x) {
     const int m = e / KP, k = e - m * KP;
     Wsm[e] = k < K ? what[m * K + k] : 0.f;
@@ -221,7 +221,7 @@ k_bwd_tail(int K, int rho, const float* __restrict__ lm, float sigma_r, const fl
   double* T = dyn;                           // W_hat^T G_W   (K x K, rows/cols >= r zero)
   double* U = dyn + K * K;                   // W_hat T
   const int tid = threadIdx.x;
-  const int r = state->rank;
+  const int r = state->planes;
   for (int e = tid; e < K * K; e += blockDim.x) {
     const int a = e / K, b = e - a * K;
     double s = 0.0;

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
   const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
   const int q0 = blockIdx.z * NQ;
   const int n = a.n;
-  const int r = a.state->rank;
+  const int r = a.state->planes;
 
   for (int e = tid; e < NQ * HH * HW; e += kConvThreads) {
     const int qi = e / (HH * HW);

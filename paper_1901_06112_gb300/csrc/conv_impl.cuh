@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
   const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
   const int q0 = blockIdx.z * NQ;
   const int n = a.n;
-  const int r = a.state->rank;
+  const int r = a.state->planes;
 
   // Image planes of this CTA's quantities (zero outside the image and for the
   // denominator quantity), then phi_0; both asynchronous.

@@ -18,11 +18,11 @@
 //      then S = X^T A X once more and a thresholded FP64 Jacobi "polish" on S
 //      (one warp) that resolves clusters of nearly equal eigenvalues, which
 //      the first-order refinement only orthonormalises;
-//   4. k_finalize (1 CTA)   sort descending, keep alpha_k > tau * alpha_max,
-//                           W_hat[m][k] = w_mk / sqrt(alpha_k) in float32 with
-//                           each eigenvector's largest-magnitude entry positive.
-// phi_k(x) = sum_m kappa(p_x, mu_m) W_hat[m][k] is then sqrt(alpha_k) v_k(x)
-// of Eq. (12).
+//   4. k_finalize (1 CTA)   sort descending, keep alpha_k > tau * alpha_max;
+//      k_wsym (K CTAs)      the symmetric factor W_hat = W_r Lambda_r^{-1/2} W_r^T
+//                           in float32 (see k_finalize).
+// phi_j(x) = sum_m kappa(p_x, mu_m) W_hat[m][j], j < K, then satisfies
+// sum_j phi_j(x) phi_j(y) = sum_{k<r} alpha_k v_k(x) v_k(y) with v_k of Eq. (12).
 #include <math.h>
 
 #include "nyf_internal.cuh"
@@ -43,6 +43,8 @@ struct EigBuf {
   double R[kMaxK * kMaxK];
   double lam[kMaxK];
   double cnA[kMaxK], cnS[kMaxK], cnR[kMaxK];   // per-column squared norms
+  int order[kMaxK];                            // eigenvalue order, descending
+  int rank;
   int bad;
 };
 
@@ -377,58 +379,62 @@ __global__ void k_polish(int K, int src, EigBuf* b) {
   for (int i = lane; i < K; i += 32) b->lam[i] = Sm[i * ld + i];
 }
 
-// ---- 4. sort, truncate, factor
-__global__ void k_finalize(int K, int src, double tau, EigBuf* b, float* __restrict__ what,
-                           double* __restrict__ alphas_out, int* __restrict__ rank_out,
-                           DevState* state) {
+// ---- 4. sort and truncate (1 CTA), then the symmetric factor (K CTAs).
+//
+// Any W_hat with W_hat W_hat^T = A_r^+ gives the same K-hat = E A_r^+ E^T and
+// hence the same filter.  The library uses the symmetric one,
+//     W_hat = W_r Lambda_r^{-1/2} W_r^T = A_r^{-1/2},
+// which is unique (no eigenvector sign or rotation freedom) and the closest
+// factor to the identity: with well-separated landmarks A is near I and each
+// feature stays close to one landmark's kernel column, so the sum over modes
+// in Eqs. (14)-(15) does not cancel large terms (it does with the eigenvector
+// factor, whose rounding then dominates the result in low precision).
+__global__ void k_finalize(int K, double tau, EigBuf* b, double* __restrict__ alphas_out,
+                           int* __restrict__ rank_out, DevState* state) {
   __shared__ double lam[kMaxK];
-  __shared__ int order[kMaxK];
-  __shared__ double sgn[kMaxK];
-  __shared__ int rsh;
   const int tid = threadIdx.x;
-  const double* X = b->X[src];
   if (tid < K) lam[tid] = b->lam[tid];
   __syncthreads();
   if (tid < K) {                                  // stable descending rank of each eigenvalue
     const double v = lam[tid];
     int rk = 0;
     for (int q = 0; q < K; ++q) rk += (lam[q] > v) || (lam[q] == v && q < tid);
-    order[rk] = tid;
+    b->order[rk] = tid;
   }
   __syncthreads();
   if (tid == 0) {
-    const double amax = lam[order[0]];
+    const double amax = lam[b->order[0]];
     int r = 0;
     if (b->bad == 0 && amax > 0.0 && isfinite(amax))
-      while (r < K && lam[order[r]] > tau * amax) ++r;
+      while (r < K && lam[b->order[r]] > tau * amax) ++r;
+    b->rank = r;
     state->rank = r;
+    state->planes = r > 0 ? K : 0;
     if (rank_out) *rank_out = r;
     if (r == 0) set_status(state, NYF_ERR_NUMERIC);
-    rsh = r;
   }
   if (tid < K) {
-    const double a = lam[order[tid]];
+    const double a = lam[b->order[tid]];
     state->alpha[tid] = a;
     if (alphas_out) alphas_out[tid] = a;
-    const int col = order[tid];                   // sign: largest-magnitude entry positive
-    int arg = 0;
-    double best = -1.0;
-    for (int m = 0; m < K; ++m) {
-      const double v = fabs(X[m * K + col]);
-      if (v > best) { best = v; arg = m; }
-    }
-    sgn[tid] = X[arg * K + col] < 0.0 ? -1.0 : 1.0;
+  }
+}
+
+// W_hat[m][j] = sum_{k < r} w_m,k w_j,k / sqrt(alpha_k)  (FP64, one column per CTA)
+__global__ void k_wsym(int K, int src, const EigBuf* b, float* __restrict__ what) {
+  const int j = blockIdx.x, m = threadIdx.x;
+  __shared__ double cj[kMaxK];
+  const double* X = b->X[src];
+  const int r = b->rank;
+  if (m < r) {
+    const int col = b->order[m];
+    cj[m] = X[j * K + col] / sqrt(b->lam[col]);
   }
   __syncthreads();
-  const int r = rsh;
-  for (int e = tid; e < K * K; e += blockDim.x) {
-    const int m = e / K, k = e - m * K;
-    float w = 0.f;
-    if (k < r) {
-      const int col = order[k];
-      w = (float)(sgn[k] * X[m * K + col] / sqrt(lam[col]));
-    }
-    what[m * K + k] = w;
+  if (m < K) {
+    double s = 0.0;
+    for (int k = 0; k < r; ++k) s = fma(X[m * K + b->order[k]], cj[k], s);
+    what[m * K + j] = (float)s;
   }
 }
 
@@ -475,8 +481,9 @@ cudaError_t launch_eig(const float* landmarks, int K, int rho, float sigma_r, do
   if (e != cudaSuccess) return e;
   k_polish<<<1, 32, psmem, st>>>(K, src, b);
   count_launches(3);
-  k_finalize<<<1, kMaxK, 0, st>>>(K, src, tau, b, what, alphas_out, rank_out, state);
-  count_launches(1);
+  k_finalize<<<1, kMaxK, 0, st>>>(K, tau, b, alphas_out, rank_out, state);
+  k_wsym<<<K, kMaxK, 0, st>>>(K, src, b, what);
+  count_launches(2);
   return cudaGetLastError();
 }
 

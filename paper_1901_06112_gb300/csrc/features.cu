@@ -140,7 +140,7 @@ k_features(const float* __restrict__ guide, int64_t N, int rho, const float* __r
   for (int e = threadIdx.x; e < K * rho; e += blockDim.x) mu[e] = lm[e];
   stage_what(what, K, Wsm);
   __syncthreads();
-  const int r = state->rank;
+  const int r = state->planes;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x * 2;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x * 2; base < N; base += stride) {
     const int64_t i0 = base + threadIdx.x, i1 = i0 + blockDim.x;
@@ -200,7 +200,7 @@ k_features_nlm(const float* __restrict__ f, int H, int W, int n, int r, const fl
   float e[KB];
 #pragma unroll
   for (int m = 0; m < KB; ++m) e[m] = (m < K) ? expf(-d2[m] * inv2s2) : 0.f;
-  emit_phi<KB, BF16>(e, K, state->rank, Wsm, phi, (int64_t)H * W, (int64_t)y * W + x);
+  emit_phi<KB, BF16>(e, K, state->planes, Wsm, phi, (int64_t)H * W, (int64_t)y * W + x);
 }
 
 template <int KB, int RB, bool BF16>

@@ -20,6 +20,8 @@ constexpr int kKmeansThreads = 256;
 struct DevState {
   int status;                 // sticky nyf_status
   int rank;                   // kept modes r
+  int planes;                 // feature planes (K when r > 0, else 0)
+  int pad0;
   unsigned long long eta_small;
   double qerr;
   double alpha[kMaxK];        // eigenvalues of A, descending

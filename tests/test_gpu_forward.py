@@ -15,7 +15,7 @@ from oracle import nystrom as ny
 from oracle import pipeline as pl
 from oracle import rng
 from paper_1901_06112_gb300 import synth
-from tests._util import FP32_REL_RMSE, report, sign_fix
+from tests._util import FP32_REL_RMSE, report
 
 pytestmark = pytest.mark.gpu
 
@@ -110,10 +110,8 @@ def test_features_match_oracle(nyf, K, sigma_r, rho):
     assert r == keep.size
     a = alphas.cpu().numpy()
     assert np.allclose(a, alpha_o, rtol=0, atol=1e-12 * alpha_o[0])
-    B = ny.cross_kernel(mu.astype(np.float64), X.astype(np.float64), sigma_r)
-    Wf = sign_fix(W_o[:, keep])
-    phi_o = (B.T @ Wf) / np.sqrt(alpha_o[keep])
-    got = phi.cpu().numpy()[:r].T
+    phi_o, _, _ = ny.features_symmetric(X.astype(np.float64), mu.astype(np.float64), sigma_r, 1e-7)
+    got = phi.cpu().numpy().T
     rr, _ = report(f"features K={K} rho={rho}", got, phi_o)
     assert rr < 1e-5
 
@@ -262,7 +260,7 @@ def test_features_gram_matches_oracle(nyf, case):
     print(f"[parity] eig {case}: gpu={alphas.cpu().numpy()} oracle={alpha_o}")
     assert int(rank.cpu()) == keep.size
     assert np.allclose(alphas.cpu().numpy(), alpha_o, rtol=0, atol=1e-12 * alpha_o[0])
-    P = phi.cpu().numpy()[: keep.size].T.astype(np.float64)
+    P = phi.cpu().numpy().T.astype(np.float64)
     from oracle import bound as bd
     Kh = bd.nystrom_matrix(X.astype(np.float64), mu.astype(np.float64), sr, tau)
     r, _ = report(f"K-hat {case}", P @ P.T, Kh)

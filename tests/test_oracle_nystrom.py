@@ -111,6 +111,13 @@ def test_filter_at_equals_full_and_features_factor_khat():
     phi, alpha, keep = ny.features(f, mu, 50.0, 1e-8)
     Kh = bd.nystrom_matrix(f.reshape(-1, 3), mu, 50.0, 1e-8)
     assert np.allclose(phi @ phi.T, Kh, rtol=1e-9, atol=1e-11)
+    ps, _, _ = ny.features_symmetric(f, mu, 50.0, 1e-8)
+    assert ps.shape[1] == 7
+    assert np.allclose(ps @ ps.T, Kh, rtol=1e-9, atol=1e-11)
+    mu[3] = mu[1]                                   # rank deficient: still factors K-hat
+    ps, _, keep = ny.features_symmetric(f, mu, 50.0, 1e-8)
+    Kh = bd.nystrom_matrix(f.reshape(-1, 3), mu, 50.0, 1e-8)
+    assert keep.size < 7 and np.allclose(ps @ ps.T, Kh, rtol=1e-9, atol=1e-11)
 
 
 def test_no_mode_kept_raises():
