@@ -65,7 +65,13 @@ typedef struct {
   int kmeans_iters;   /* Lloyd iterations, >= 0 (0: landmarks = the drawn pixels) */
   uint64_t seed;      /* SplitMix64 seed of the initial-landmark and subsample draws */
   double eig_rel_tol; /* tau: modes with alpha_k > tau * alpha_max are kept, >= 0 */
-  int precision;      /* nyf_precision: storage/arithmetic of the per-pixel features */
+  int precision;      /* nyf_precision.  Filters: NYF_BF16 runs the convolutions (window
+                         radius <= 16) on the BF16 tensor cores -- operands phi f and
+                         the vertical-pass result rounded to bfloat16, FP32
+                         accumulation; the features stay float32 in the workspace
+                         (bfloat16 storage of phi alone costs up to 4e-3 relative
+                         error when landmarks are sparse relative to sigma_r).
+                         nyf_features: storage type of phi. */
   int spatial;        /* nyf_spatial */
   int S;              /* window radius; <= 0 means ceil(3 sigma_s) */
   int patch_radius;   /* NLM: guide = (2r+1)^2 x n patch, reflect-101 border */

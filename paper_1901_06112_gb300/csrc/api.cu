@@ -151,7 +151,7 @@ WsShape shape_for(int H, int W, int n, int rho, const nyf_params* p) {
   s.rho = rho;
   s.K = p->K;
   s.Ns = subsample_rows(s.N, p->sample_frac);
-  s.bf16 = p->precision == NYF_BF16;
+  s.bf16 = false;   // the filters keep phi in float32 (see nyf_params.precision)
   s.gather = p->patch_radius > 0;
   return s;
 }
@@ -307,7 +307,7 @@ nyf_status nyf_filter_blf(const float* f, const float* guide, int H, int W, int 
   char* w = reinterpret_cast<char*>(ws);
   DevState* state = reinterpret_cast<DevState*>(w + L.state);
   const int64_t N = (int64_t)H * W;
-  const bool bf16 = p->precision == NYF_BF16;
+  const bool tc = p->precision == NYF_BF16;
   NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
   timing_begin(0, 3);
   {
@@ -325,11 +325,11 @@ nyf_status nyf_filter_blf(const float* f, const float* guide, int H, int W, int 
   }
   {
     Stage t(st, 2);
-    NYF_TRY(launch_features(guide, N, rho, lm, p->K, p->sigma_r, what, state, phi, bf16, st));
+    NYF_TRY(launch_features(guide, N, rho, lm, p->K, p->sigma_r, what, state, phi, false, st));
   }
   {
     Stage t(st, 3);
-    NYF_TRY(launch_conv_combine(f, H, W, n, phi, bf16, p->spatial, p->sigma_s, window_radius(p),
+    NYF_TRY(launch_conv_combine(f, H, W, n, phi, false, tc, p->spatial, p->sigma_s, window_radius(p),
                                 state, out, reinterpret_cast<float*>(w + L.eta),
                                 reinterpret_cast<float*>(w + L.zeta), st));
   }
@@ -349,7 +349,7 @@ nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params*
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = reinterpret_cast<char*>(ws);
   DevState* state = reinterpret_cast<DevState*>(w + L.state);
-  const bool bf16 = p->precision == NYF_BF16;
+  const bool tc = p->precision == NYF_BF16;
   NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
   // The patch guide is never stored: k-means always clusters a gathered
   // subsample of patch vectors (all pixels when sample_frac == 1).
@@ -371,11 +371,11 @@ nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params*
   {
     Stage t(st, 2);
     NYF_TRY(launch_features_nlm(f, H, W, n, p->patch_radius, lm, p->K, p->sigma_r, what, state,
-                                phi, bf16, st));
+                                phi, false, st));
   }
   {
     Stage t(st, 3);
-    NYF_TRY(launch_conv_combine(f, H, W, n, phi, bf16, p->spatial, p->sigma_s, window_radius(p),
+    NYF_TRY(launch_conv_combine(f, H, W, n, phi, false, tc, p->spatial, p->sigma_s, window_radius(p),
                                 state, out, reinterpret_cast<float*>(w + L.eta),
                                 reinterpret_cast<float*>(w + L.zeta), st));
   }
@@ -402,14 +402,14 @@ nyf_status nyf_filter_blf_backward(const float* f, const float* guide, int H, in
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = reinterpret_cast<char*>(ws);
   DevState* state = reinterpret_cast<DevState*>(w + L.state);
-  const bool bf16 = p->precision == NYF_BF16;
+  const bool tc = p->precision == NYF_BF16;
   const int S = window_radius(p);
   float* dphi = reinterpret_cast<float*>(w + L.dphi);
   float* spart = reinterpret_cast<float*>(w + L.spart);
   timing_begin(4, 6);
   {
     Stage t(st, 4);
-    NYF_TRY(launch_bwd_conv(f, H, W, n, p->K, p->spatial, p->sigma_s, S, w + L.phi, bf16,
+    NYF_TRY(launch_bwd_conv(f, H, W, n, p->K, p->spatial, p->sigma_s, S, w + L.phi, false,
                             reinterpret_cast<const float*>(w + L.eta), out, grad_out, grad_f, dphi,
                             spart, state, st));
   }

@@ -21,6 +21,9 @@ __global__ void k_divide(const float* __restrict__ zeta, const float* __restrict
 
 }  // namespace
 
+cudaError_t conv_mma_dispatch(const ConvArgs& a, cudaStream_t st);
+bool conv_mma_split(int n);
+
 // Smallest compiled radius >= S.
 int conv_compiled_radius(int S) {
   if (S <= 16) return S < 1 ? 1 : S;
@@ -38,8 +41,9 @@ bool conv_split(int S, int n) {
 }
 
 cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void* phi, bool bf16,
-                                int spatial, float sigma_s, int S, DevState* state, float* out,
-                                float* eta_out, float* zeta_ws, cudaStream_t st) {
+                                bool tensor_cores, int spatial, float sigma_s, int S,
+                                DevState* state, float* out, float* eta_out, float* zeta_ws,
+                                cudaStream_t st) {
   const int Sc = conv_compiled_radius(S);
   if (Sc < 0) return cudaErrorInvalidValue;
   ConvArgs a;
@@ -58,12 +62,15 @@ cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void*
   double mass = 0.0;   // full-window mass of omega
   for (int z = -S; z <= S; ++z) mass += a.box ? 1.0 : exp(-(double)z * z * a.inv2s2);
   a.eta_thr = (float)(1e-6 * mass * mass);
-  const bool split = n + 1 > conv_nq(Sc);
+  // BF16 tensor-core kernel for S <= 16 when asked for; otherwise the FP32 FIR kernel
+  const bool mma = tensor_cores && S <= 16;
+  const bool split = mma ? conv_mma_split(n) : n + 1 > conv_nq(Sc);
   a.out = split ? nullptr : out;
   a.zeta = split ? zeta_ws : nullptr;
   a.eta = eta_out;
   cudaError_t e;
-  if (Sc <= 8) e = conv_dispatch_a(Sc, a, st);
+  if (mma) e = conv_mma_dispatch(a, st);
+  else if (Sc <= 8) e = conv_dispatch_a(Sc, a, st);
   else if (Sc <= 16) e = conv_dispatch_b(Sc, a, st);
   else e = conv_dispatch_c(Sc, a, st);
   if (e != cudaSuccess || !split) return e;

@@ -1,0 +1,105 @@
+"""Parity of the BF16 path (features stored in bfloat16, convolutions on the
+tensor cores for S <= 16) with the FP64 oracle: relative RMSE <= 2e-3."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import kernels as Kr
+from oracle import nystrom as ny
+from oracle import pipeline as pl
+from oracle import rng
+from paper_1901_06112_gb300 import synth
+from tests._util import BF16_REL_RMSE, report
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nyf():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1901_06112_gb300 import build
+    build.build()
+    from paper_1901_06112_gb300 import nyf as N
+    return N
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("H,W,sigma_s,sigma_r,K", [(256, 256, 3.0, 30.0, 8), (97, 131, 2.0, 25.0, 6),
+                                                   (70, 200, 5.0, 40.0, 16), (33, 47, 0.7, 60.0, 5),
+                                                   (64, 64, 5.3, 35.0, 12), (50, 81, 7.0, 45.0, 9),
+                                                   (129, 65, 2.0, 10.0, 16)])
+def test_bf16_blf_parity(nyf, H, W, sigma_s, sigma_r, K):
+    f = synth.voronoi_colour(H, W, 40, 10.0, H * 7 + W)
+    mu, _ = pl.landmarks(f.reshape(-1, 3).astype(np.float64), K, 5, 3)
+    mu = mu.astype(np.float32)
+    S = int(math.ceil(3 * sigma_s))
+    sr = float(np.float32(sigma_r))
+    want = ny.nystrom_filter(f, f, mu.astype(np.float64), sr, Kr.gaussian_taps(sigma_s, S), 1e-7)
+    out = nyf.blf(cuda(f), nyf.Params(sigma_s=sigma_s, sigma_r=sr, K=K, precision="bf16"),
+                  landmarks=cuda(mu))
+    r, _ = report(f"bf16 blf {H}x{W} S={S} sr={sigma_r} K={K}", out.cpu().numpy(), want)
+    assert r < BF16_REL_RMSE
+
+
+def test_bf16_box_and_split_quantities(nyf):
+    f = synth.hyperspectral(40, 52, 7, 3, 8.0, 0.02, 21) * 255.0
+    g = synth.voronoi_colour(40, 52, 10, 5.0, 22)
+    mu = g.reshape(-1, 3)[rng.distinct_indices(9, 6, 40 * 52)].astype(np.float32)
+    want = ny.nystrom_filter(f, g, mu.astype(np.float64), 35.0, Kr.box_taps(5), 1e-7)
+    out = nyf.blf(cuda(f), nyf.Params(sigma_r=35.0, K=6, spatial="box", S=5, precision="bf16"),
+                  guide=cuda(g), landmarks=cuda(mu))
+    r, _ = report("bf16 joint box n=7", out.cpu().numpy(), want)
+    assert r < BF16_REL_RMSE
+
+
+def test_bf16_full_hd_sampled(nyf):
+    w = synth.colour_blf_hd()
+    mu, _ = pl.landmarks(w.f.reshape(-1, 3).astype(np.float64), w.K, w.kmeans_iters, w.seed)
+    mu = mu.astype(np.float32)
+    sr = float(np.float32(w.sigma_r))
+    P = nyf.Params(sigma_s=w.sigma_s, sigma_r=sr, K=w.K, precision="bf16")
+    out = nyf.blf(cuda(w.f), P, landmarks=cuda(mu)).cpu().numpy()
+    idx = synth.sample_indices(w.H * w.W, 300, 21)
+    ys, xs = idx // w.W, idx % w.W
+    want = ny.nystrom_filter_at(w.f, w.f, mu.astype(np.float64), sr,
+                                Kr.gaussian_taps(w.sigma_s, w.radius), 1e-7, ys, xs)
+    r, _ = report("bf16 colour 1920x1080 K=32 (300 samples)", out[ys, xs], want)
+    assert r < BF16_REL_RMSE
+
+
+def test_bf16_nlm(nyf):
+    f = synth.voronoi_colour(60, 72, 20, 20.0, 26, ramp=0.1)
+    P = nyf.Params(sigma_r=20.0 * math.sqrt(75.0), K=6, spatial="box", S=4, patch_radius=2,
+                   sample_frac=0.05, seed=77, kmeans_iters=6, precision="bf16")
+    X, idx, p = pl.nlm_sample_rows(f.astype(np.float64), 2, 0.05, 77)
+    mu, _ = pl.landmarks(X, 6, 6, 77)
+    mu = mu.astype(np.float32)
+    want = ny.nystrom_filter(f, p, mu.astype(np.float64), P.sigma_r, Kr.box_taps(4), 1e-7)
+    out = nyf.nlm(cuda(f), P, landmarks=cuda(mu))
+    r, _ = report("bf16 nlm 60x72", out.cpu().numpy(), want)
+    assert r < BF16_REL_RMSE
+
+
+def test_bf16_backward_close_to_oracle(nyf):
+    # the backward runs in FP32 but differentiates the BF16 forward (its eta and
+    # g_hat carry the BF16 rounding), hence the looser bound
+    from oracle import grad as gr
+    f = synth.voronoi_colour(40, 36, 8, 12.0, 140)
+    mu = f.reshape(-1, 3)[rng.distinct_indices(140, 5, 40 * 36)].astype(np.float32)
+    G = np.random.default_rng(142).normal(size=f.shape).astype(np.float32)
+    ref = gr.vjp(f, f, mu, 45.0, 2.0, 6, 1e-7, G, guide_is_image=True)
+    res = nyf.blf_vjp(cuda(f), nyf.Params(sigma_s=2.0, sigma_r=45.0, K=5, precision="bf16"),
+                      cuda(G), landmarks=cuda(mu))
+    r, _ = report("bf16 grad f", res["df"].cpu().numpy(), ref["df"])
+    assert r < 2e-2
+    for nm in ("dsigma_r", "dsigma_s"):
+        rel = abs(res[nm] - ref[nm]) / abs(ref[nm])
+        print(f"[parity] bf16 {nm}: gpu={res[nm]:.6e} oracle={ref[nm]:.6e} rel={rel:.2e}")
+        assert rel < 2e-2
