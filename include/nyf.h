@@ -57,6 +57,13 @@ typedef enum {
 typedef enum { NYF_FP32 = 0, NYF_BF16 = 1 } nyf_precision;
 typedef enum { NYF_GAUSSIAN = 0, NYF_BOX = 1 } nyf_spatial;
 
+/* Convolution kernel variant (nyf_params.conv_tile).  AUTO: tensor cores for
+ * NYF_BF16, wide FP32 tiles otherwise.  WIDE / NARROW: FP32 FIR kernel with
+ * 32 x 96 / 32 x 64 output tiles (radius <= 16; larger radii have one tile
+ * shape).  TENSOR: BF16 tensor-core kernel (radius <= 16, else WIDE).  The
+ * autotuner (paper_1901_06112_gb300.tune) picks one per radius by timing. */
+typedef enum { NYF_TILE_AUTO = 0, NYF_TILE_WIDE = 1, NYF_TILE_NARROW = 2, NYF_TILE_TENSOR = 3 } nyf_tile;
+
 /* Filter parameters (Sec. IV setup; Algorithm 1's m0 is K). */
 typedef struct {
   float sigma_s;      /* spatial Gaussian std; unused for NYF_BOX unless S <= 0 */
@@ -76,6 +83,7 @@ typedef struct {
   int S;              /* window radius; <= 0 means ceil(3 sigma_s) */
   int patch_radius;   /* NLM: guide = (2r+1)^2 x n patch, reflect-101 border */
   float sample_frac;  /* fraction of pixels k-means clusters, (0, 1] */
+  int conv_tile;      /* nyf_tile: convolution kernel variant */
 } nyf_params;
 
 /* Device-side results of the last call on a workspace (nyf_get_stats). */
@@ -187,6 +195,46 @@ nyf_status nyf_filter_blf_backward(const float* f, const float* guide, int H, in
                                    int rho, const nyf_params* params, const float* out,
                                    const float* grad_out, float* grad_f, float* grad_guide,
                                    float* grad_sigma, void* ws, size_t ws_bytes, void* stream);
+
+/* ---- Batched filtering of images of uneven sizes (one workload, one call).
+ * Image b of the batch is the H_b x W_b x n HWC block starting at element
+ * items[b].offset of the packed buffers f / out / grad_out / grad_f (device);
+ * items is a host array read during the call.  Each image uses its own
+ * sigma_s, sigma_r (and conv_tile unless NYF_TILE_AUTO) and the shared
+ * fields of *params; landmarks come from k-means per image.  The images are
+ * spread over a small pool of internal streams of the current device, forked
+ * from and joined back to `stream` with events, so the whole call can be
+ * captured into a CUDA graph and replayed.  Do not issue batched calls on the
+ * same device from several host threads at once (they share the pool). */
+typedef struct {
+  int64_t offset;   /* first element of image b in the packed buffers */
+  int H, W;
+  float sigma_s, sigma_r;
+  int conv_tile;    /* nyf_tile for this image, or NYF_TILE_AUTO for params->conv_tile */
+  int reserved;
+} nyf_batch_item;
+
+/* Workspace bytes for the batch (per-image slices), 0 if invalid. */
+size_t nyf_batched_workspace_size(const nyf_batch_item* items, int B, int n,
+                                  const nyf_params* params);
+
+/* Forward of every image (as nyf_filter_blf with guide = image). */
+nyf_status nyf_filter_blf_batched(const float* f, const nyf_batch_item* items, int B, int n,
+                                  const nyf_params* params, float* out, void* ws, size_t ws_bytes,
+                                  void* stream);
+
+/* Backward of every image (as nyf_filter_blf_backward), after the batched
+ * forward on the same workspace.  grad_sigma: 2 B floats (device),
+ * [dL/d sigma_r, dL/d sigma_s] per image. */
+nyf_status nyf_filter_blf_batched_backward(const float* f, const nyf_batch_item* items, int B,
+                                           int n, const nyf_params* params, const float* out,
+                                           const float* grad_out, float* grad_f,
+                                           float* grad_sigma, void* ws, size_t ws_bytes,
+                                           void* stream);
+
+/* nyf_get_stats of image b of a batch. */
+nyf_status nyf_batched_stats(const void* ws, const nyf_batch_item* items, int B, int n,
+                             const nyf_params* params, int b, nyf_stats* out, void* stream);
 
 /* Copies the device-side results of the last call on `ws` to *out.  This is
  * the one call that synchronises `stream`. */

@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "NYF_OK", 1: "NYF_ERR_INVALID_ARG", 2: "NYF_ERR_UNSUPPORTED",
                 6: "NYF_ERR_TIMEOUT"}
 FP32, BF16 = 0, 1
 GAUSSIAN, BOX = 0, 1
+TILE_AUTO, TILE_WIDE, TILE_NARROW, TILE_TENSOR = 0, 1, 2, 3
 MAX_K, MAX_RHO, MAX_S, MAX_CHANNELS = 64, 160, 32, 64
 
 
@@ -24,7 +25,7 @@ class NyfParams(C.Structure):
     _fields_ = [("sigma_s", C.c_float), ("sigma_r", C.c_float), ("K", C.c_int),
                 ("kmeans_iters", C.c_int), ("seed", C.c_uint64), ("eig_rel_tol", C.c_double),
                 ("precision", C.c_int), ("spatial", C.c_int), ("S", C.c_int),
-                ("patch_radius", C.c_int), ("sample_frac", C.c_float)]
+                ("patch_radius", C.c_int), ("sample_frac", C.c_float), ("conv_tile", C.c_int)]
 
 
 class NyfStats(C.Structure):
@@ -34,9 +35,9 @@ class NyfStats(C.Structure):
                 ("grad_sigma_s", C.c_float)]
 
 
-class NyfBatchDesc(C.Structure):
+class NyfBatchItem(C.Structure):
     _fields_ = [("offset", C.c_int64), ("H", C.c_int), ("W", C.c_int), ("sigma_s", C.c_float),
-                ("sigma_r", C.c_float), ("S", C.c_int), ("K", C.c_int)]
+                ("sigma_r", C.c_float), ("conv_tile", C.c_int), ("reserved", C.c_int)]
 
 
 _P = C.c_void_p
@@ -62,12 +63,16 @@ _SIGNATURES = {
     "nyf_features_static": (C.c_int, [_P, C.c_int64, C.c_int, _P, C.c_int, C.c_float, C.c_double,
                                       C.c_int, _P, _P, _P, _P]),
 }
-OPTIONAL = {
-    "nyf_batched_workspace_size": (C.c_size_t, [_P, C.c_int, C.c_int, C.c_int, C.c_int]),
-    "nyf_filter_blf_batched": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
-                                         C.c_int, C.c_uint64, _P, _P, _P, _P, _P, _P, C.c_size_t,
-                                         _P]),
-}
+OPTIONAL = {}
+_SIGNATURES.update({
+    "nyf_batched_workspace_size": (C.c_size_t, [_P, C.c_int, C.c_int, C.POINTER(NyfParams)]),
+    "nyf_filter_blf_batched": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(NyfParams), _P, _P,
+                                         C.c_size_t, _P]),
+    "nyf_filter_blf_batched_backward": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(NyfParams),
+                                                  _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "nyf_batched_stats": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(NyfParams), C.c_int,
+                                    C.POINTER(NyfStats), _P]),
+})
 
 _lib = None
 

@@ -5,8 +5,10 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "nyf_internal.cuh"
 
@@ -65,7 +67,8 @@ struct Stage {
   cudaStream_t st;
   int id;
   bool on;
-  Stage(cudaStream_t s, int i) : st(s), id(i), on(g_timing.load() != 0 && g_events_ready) {
+  Stage(cudaStream_t s, int i, bool timed = true)
+      : st(s), id(i), on(timed && g_timing.load() != 0 && g_events_ready) {
     if (on) cudaEventRecord(g_ev[id][0], st);
   }
   ~Stage() {
@@ -93,6 +96,12 @@ int64_t subsample_rows(int64_t N, float frac) {
   return v;
 }
 
+int resolve_tile(const nyf_params* p) {
+  if (p->conv_tile == NYF_TILE_AUTO)
+    return p->precision == NYF_BF16 ? NYF_TILE_TENSOR : NYF_TILE_WIDE;
+  return p->conv_tile;
+}
+
 nyf_status check_params(const nyf_params* p, int n) {
   if (!p) return NYF_ERR_INVALID_ARG;
   if (!(p->sigma_r > 0.f) || !isfinite(p->sigma_r)) return NYF_ERR_INVALID_ARG;
@@ -111,6 +120,7 @@ nyf_status check_params(const nyf_params* p, int n) {
   if (S < 1) return NYF_ERR_INVALID_ARG;
   if (S > NYF_MAX_S) return NYF_ERR_UNSUPPORTED;
   if (p->patch_radius < 0) return NYF_ERR_INVALID_ARG;
+  if (p->conv_tile < NYF_TILE_AUTO || p->conv_tile > NYF_TILE_TENSOR) return NYF_ERR_INVALID_ARG;
   return NYF_OK;
 }
 
@@ -186,6 +196,205 @@ nyf_status stage_landmarks(const float* X_full, int64_t N, int rho, const nyf_pa
                         reinterpret_cast<float*>(w + L.km_part),
                         reinterpret_cast<float*>(w + L.km_qpart), state, st));
   return NYF_OK;
+}
+
+}  // namespace
+
+namespace {
+
+nyf_status blf_impl(const float* f, const float* guide, int H, int W, int n, int rho,
+                    const nyf_params* p, const float* landmarks, float* out, void* ws,
+                    size_t ws_bytes, void* stream, bool timed) {
+  if (!p || p->patch_radius != 0) return NYF_ERR_INVALID_ARG;
+  if (!guide) {
+    if (rho != n) return NYF_ERR_INVALID_ARG;
+    guide = f;
+  }
+  nyf_status s = check_filter(f, H, W, n, rho, p, out);
+  if (s != NYF_OK) return s;
+  if (!aligned4(guide)) return NYF_ERR_INVALID_ARG;
+  const WsLayout L = ws_layout(shape_for(H, W, n, rho, p));
+  if (!ws_ok(ws, ws_bytes, L.total)) return NYF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  DevState* state = reinterpret_cast<DevState*>(w + L.state);
+  const int64_t N = (int64_t)H * W;
+  const int tile = resolve_tile(p);
+  NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
+  if (timed) timing_begin(0, 3);
+  {
+    Stage t(st, 0, timed);
+    s = stage_landmarks(guide, N, rho, p, landmarks, w, L, false, f, H, W, n, st);
+  }
+  if (s != NYF_OK) return s;
+  const float* lm = reinterpret_cast<const float*>(w + L.landmarks);
+  float* what = reinterpret_cast<float*>(w + L.what);
+  void* phi = w + L.phi;
+  {
+    Stage t(st, 1, timed);
+    NYF_TRY(launch_eig(lm, p->K, rho, p->sigma_r, p->eig_rel_tol, what, nullptr, nullptr, state,
+                       w + L.eig, st));
+  }
+  {
+    Stage t(st, 2, timed);
+    NYF_TRY(launch_features(guide, N, rho, lm, p->K, p->sigma_r, what, state, phi, false, st));
+  }
+  {
+    Stage t(st, 3, timed);
+    NYF_TRY(launch_conv_combine(f, H, W, n, phi, false, tile, p->spatial, p->sigma_s, window_radius(p),
+                                state, out, reinterpret_cast<float*>(w + L.eta),
+                                reinterpret_cast<float*>(w + L.zeta), st));
+  }
+  return NYF_OK;
+}
+
+nyf_status blf_backward_impl(const float* f, const float* guide, int H, int W, int n, int rho,
+                             const nyf_params* p, const float* out, const float* grad_out,
+                             float* grad_f, float* grad_guide, float* grad_sigma, void* ws,
+                             size_t ws_bytes, void* stream, bool timed) {
+  if (!p || p->patch_radius != 0) return NYF_ERR_INVALID_ARG;
+  const bool tied = guide == nullptr || guide == f;
+  if (tied) {
+    if (rho != n) return NYF_ERR_INVALID_ARG;
+    guide = f;
+  }
+  nyf_status s = check_filter(f, H, W, n, rho, p, out);
+  if (s != NYF_OK) return s;
+  if (!grad_out || !grad_f || !grad_sigma || !aligned4(grad_out) || !aligned4(grad_f) ||
+      !aligned4(grad_sigma) || (!tied && (!grad_guide || !aligned4(grad_guide))))
+    return NYF_ERR_INVALID_ARG;
+  const WsLayout L = ws_layout(shape_for(H, W, n, rho, p));
+  if (!ws_ok(ws, ws_bytes, L.total)) return NYF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  DevState* state = reinterpret_cast<DevState*>(w + L.state);
+  const int tile = resolve_tile(p);
+  const int S = window_radius(p);
+  float* dphi = reinterpret_cast<float*>(w + L.dphi);
+  float* spart = reinterpret_cast<float*>(w + L.spart);
+  if (timed) timing_begin(4, 6);
+  {
+    Stage t(st, 4, timed);
+    NYF_TRY(launch_bwd_conv(f, H, W, n, p->K, p->spatial, p->sigma_s, S, w + L.phi, false,
+                            reinterpret_cast<const float*>(w + L.eta), out, grad_out, grad_f, dphi,
+                            spart, state, st));
+  }
+  {
+    Stage t(st, 5, timed);
+    NYF_TRY(launch_bwd_features(f, guide, H, W, n, rho, reinterpret_cast<const float*>(w + L.landmarks),
+                                p->K, p->sigma_r, S, reinterpret_cast<const float*>(w + L.what),
+                                dphi, grad_f, tied ? nullptr : grad_guide,
+                                reinterpret_cast<float*>(w + L.gpart), spart,
+                                reinterpret_cast<double*>(w + L.gw), w + L.eig, grad_sigma, state,
+                                st));
+  }
+  return NYF_OK;
+}
+
+// ---- batched filtering: images spread over a pool of internal streams, forked
+// from and joined back to the caller's stream with events (capturable).
+constexpr int kPool = 8;
+constexpr int kMaxDevices = 64;
+struct StreamPool {
+  bool ready = false;
+  cudaStream_t s[kPool];
+  cudaEvent_t fork;
+  cudaEvent_t join[kPool];
+};
+StreamPool g_pools[kMaxDevices];
+std::mutex g_pool_mu;
+
+cudaError_t device_pool(StreamPool** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  StreamPool& P = g_pools[dev];
+  if (!P.ready) {
+    for (int i = 0; i < kPool; ++i) {
+      if ((e = cudaStreamCreateWithFlags(&P.s[i], cudaStreamNonBlocking)) != cudaSuccess) return e;
+      if ((e = cudaEventCreateWithFlags(&P.join[i], cudaEventDisableTiming)) != cudaSuccess) return e;
+    }
+    if ((e = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+    P.ready = true;
+  }
+  *out = &P;
+  return cudaSuccess;
+}
+
+nyf_params item_params(const nyf_params* p, const nyf_batch_item& it) {
+  nyf_params q = *p;
+  q.sigma_s = it.sigma_s;
+  q.sigma_r = it.sigma_r;
+  if (it.conv_tile != NYF_TILE_AUTO) q.conv_tile = it.conv_tile;
+  return q;
+}
+
+// Workspace offset of every image (256-byte aligned slices) and the total.
+bool batch_layout(const nyf_batch_item* items, int B, int n, const nyf_params* p, size_t* offs,
+                  size_t* total) {
+  size_t o = 0;
+  for (int b = 0; b < B; ++b) {
+    const nyf_params q = item_params(p, items[b]);
+    const size_t sz = nyf_workspace_size(items[b].H, items[b].W, n, n, &q);
+    if (sz == 0) return false;
+    if (offs) offs[b] = o;
+    o = (o + sz + 255) & ~(size_t)255;
+  }
+  *total = o;
+  return true;
+}
+
+// Longest-processing-time assignment of images to pool streams.
+void assign_streams(const nyf_batch_item* items, int B, int* stream_of) {
+  long long load[kPool] = {0};
+  std::vector<int> order(B);
+  for (int b = 0; b < B; ++b) order[b] = b;
+  std::sort(order.begin(), order.end(), [&](int a, int c) {
+    return (long long)items[a].H * items[a].W > (long long)items[c].H * items[c].W;
+  });
+  for (int b : order) {
+    int best = 0;
+    for (int i = 1; i < kPool; ++i)
+      if (load[i] < load[best]) best = i;
+    stream_of[b] = best;
+    load[best] += (long long)items[b].H * items[b].W;
+  }
+}
+
+template <typename Fn>
+nyf_status run_batched(const nyf_batch_item* items, int B, int n, const nyf_params* p, void* ws,
+                       size_t ws_bytes, void* stream, Fn&& per_image) {
+  if (!items || B < 1 || !p) return NYF_ERR_INVALID_ARG;
+  std::vector<size_t> offs(B);
+  size_t total = 0;
+  if (!batch_layout(items, B, n, p, offs.data(), &total)) return NYF_ERR_INVALID_ARG;
+  if (!ws_ok(ws, ws_bytes, total)) return NYF_ERR_WORKSPACE;
+  for (int b = 0; b < B; ++b)
+    if (items[b].offset < 0 || items[b].H < 1 || items[b].W < 1) return NYF_ERR_INVALID_ARG;
+  StreamPool* P = nullptr;
+  if (device_pool(&P) != cudaSuccess) return NYF_ERR_CUDA;
+  std::vector<int> sof(B);
+  assign_streams(items, B, sof.data());
+  bool used[kPool] = {false};
+  for (int b = 0; b < B; ++b) used[sof[b]] = true;
+  cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
+  NYF_TRY(cudaEventRecord(P->fork, caller));
+  for (int i = 0; i < kPool; ++i)
+    if (used[i]) NYF_TRY(cudaStreamWaitEvent(P->s[i], P->fork, 0));
+  nyf_status status = NYF_OK;
+  for (int b = 0; b < B && status == NYF_OK; ++b) {
+    const nyf_params q = item_params(p, items[b]);
+    status = per_image(b, q, reinterpret_cast<char*>(ws) + offs[b], total - offs[b], P->s[sof[b]]);
+  }
+  // join every used stream back even after an error, so the caller's stream stays ordered
+  for (int i = 0; i < kPool; ++i)
+    if (used[i]) {
+      if (cudaEventRecord(P->join[i], P->s[i]) != cudaSuccess) return NYF_ERR_CUDA;
+      if (cudaStreamWaitEvent(caller, P->join[i], 0) != cudaSuccess) return NYF_ERR_CUDA;
+    }
+  return status;
 }
 
 }  // namespace
@@ -293,47 +502,7 @@ nyf_status nyf_features(const float* guide, int64_t N, int rho, const float* lan
 nyf_status nyf_filter_blf(const float* f, const float* guide, int H, int W, int n, int rho,
                           const nyf_params* p, const float* landmarks, float* out, void* ws,
                           size_t ws_bytes, void* stream) {
-  if (!p || p->patch_radius != 0) return NYF_ERR_INVALID_ARG;
-  if (!guide) {
-    if (rho != n) return NYF_ERR_INVALID_ARG;
-    guide = f;
-  }
-  nyf_status s = check_filter(f, H, W, n, rho, p, out);
-  if (s != NYF_OK) return s;
-  if (!aligned4(guide)) return NYF_ERR_INVALID_ARG;
-  const WsLayout L = ws_layout(shape_for(H, W, n, rho, p));
-  if (!ws_ok(ws, ws_bytes, L.total)) return NYF_ERR_WORKSPACE;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  char* w = reinterpret_cast<char*>(ws);
-  DevState* state = reinterpret_cast<DevState*>(w + L.state);
-  const int64_t N = (int64_t)H * W;
-  const bool tc = p->precision == NYF_BF16;
-  NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
-  timing_begin(0, 3);
-  {
-    Stage t(st, 0);
-    s = stage_landmarks(guide, N, rho, p, landmarks, w, L, false, f, H, W, n, st);
-  }
-  if (s != NYF_OK) return s;
-  const float* lm = reinterpret_cast<const float*>(w + L.landmarks);
-  float* what = reinterpret_cast<float*>(w + L.what);
-  void* phi = w + L.phi;
-  {
-    Stage t(st, 1);
-    NYF_TRY(launch_eig(lm, p->K, rho, p->sigma_r, p->eig_rel_tol, what, nullptr, nullptr, state,
-                       w + L.eig, st));
-  }
-  {
-    Stage t(st, 2);
-    NYF_TRY(launch_features(guide, N, rho, lm, p->K, p->sigma_r, what, state, phi, false, st));
-  }
-  {
-    Stage t(st, 3);
-    NYF_TRY(launch_conv_combine(f, H, W, n, phi, false, tc, p->spatial, p->sigma_s, window_radius(p),
-                                state, out, reinterpret_cast<float*>(w + L.eta),
-                                reinterpret_cast<float*>(w + L.zeta), st));
-  }
-  return NYF_OK;
+  return blf_impl(f, guide, H, W, n, rho, p, landmarks, out, ws, ws_bytes, stream, true);
 }
 
 nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params* p,
@@ -349,7 +518,7 @@ nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params*
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = reinterpret_cast<char*>(ws);
   DevState* state = reinterpret_cast<DevState*>(w + L.state);
-  const bool tc = p->precision == NYF_BF16;
+  const int tile = resolve_tile(p);
   NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
   // The patch guide is never stored: k-means always clusters a gathered
   // subsample of patch vectors (all pixels when sample_frac == 1).
@@ -375,7 +544,7 @@ nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params*
   }
   {
     Stage t(st, 3);
-    NYF_TRY(launch_conv_combine(f, H, W, n, phi, false, tc, p->spatial, p->sigma_s, window_radius(p),
+    NYF_TRY(launch_conv_combine(f, H, W, n, phi, false, tile, p->spatial, p->sigma_s, window_radius(p),
                                 state, out, reinterpret_cast<float*>(w + L.eta),
                                 reinterpret_cast<float*>(w + L.zeta), st));
   }
@@ -386,43 +555,8 @@ nyf_status nyf_filter_blf_backward(const float* f, const float* guide, int H, in
                                    int rho, const nyf_params* p, const float* out,
                                    const float* grad_out, float* grad_f, float* grad_guide,
                                    float* grad_sigma, void* ws, size_t ws_bytes, void* stream) {
-  if (!p || p->patch_radius != 0) return NYF_ERR_INVALID_ARG;
-  const bool tied = guide == nullptr || guide == f;
-  if (tied) {
-    if (rho != n) return NYF_ERR_INVALID_ARG;
-    guide = f;
-  }
-  nyf_status s = check_filter(f, H, W, n, rho, p, out);
-  if (s != NYF_OK) return s;
-  if (!grad_out || !grad_f || !grad_sigma || !aligned4(grad_out) || !aligned4(grad_f) ||
-      !aligned4(grad_sigma) || (!tied && (!grad_guide || !aligned4(grad_guide))))
-    return NYF_ERR_INVALID_ARG;
-  const WsLayout L = ws_layout(shape_for(H, W, n, rho, p));
-  if (!ws_ok(ws, ws_bytes, L.total)) return NYF_ERR_WORKSPACE;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  char* w = reinterpret_cast<char*>(ws);
-  DevState* state = reinterpret_cast<DevState*>(w + L.state);
-  const bool tc = p->precision == NYF_BF16;
-  const int S = window_radius(p);
-  float* dphi = reinterpret_cast<float*>(w + L.dphi);
-  float* spart = reinterpret_cast<float*>(w + L.spart);
-  timing_begin(4, 6);
-  {
-    Stage t(st, 4);
-    NYF_TRY(launch_bwd_conv(f, H, W, n, p->K, p->spatial, p->sigma_s, S, w + L.phi, false,
-                            reinterpret_cast<const float*>(w + L.eta), out, grad_out, grad_f, dphi,
-                            spart, state, st));
-  }
-  {
-    Stage t(st, 5);
-    NYF_TRY(launch_bwd_features(f, guide, H, W, n, rho, reinterpret_cast<const float*>(w + L.landmarks),
-                                p->K, p->sigma_r, S, reinterpret_cast<const float*>(w + L.what),
-                                dphi, grad_f, tied ? nullptr : grad_guide,
-                                reinterpret_cast<float*>(w + L.gpart), spart,
-                                reinterpret_cast<double*>(w + L.gw), w + L.eig, grad_sigma, state,
-                                st));
-  }
-  return NYF_OK;
+  return blf_backward_impl(f, guide, H, W, n, rho, p, out, grad_out, grad_f, grad_guide, grad_sigma,
+                           ws, ws_bytes, stream, true);
 }
 
 nyf_status nyf_get_stats(const void* ws, nyf_stats* out, void* stream) {
@@ -442,6 +576,50 @@ nyf_status nyf_get_stats(const void* ws, nyf_stats* out, void* stream) {
   out->grad_sigma_r = h.grad_sigma[0];
   out->grad_sigma_s = h.grad_sigma[1];
   return NYF_OK;
+}
+
+size_t nyf_batched_workspace_size(const nyf_batch_item* items, int B, int n,
+                                  const nyf_params* p) {
+  if (!items || B < 1 || !p) return 0;
+  size_t total = 0;
+  return batch_layout(items, B, n, p, nullptr, &total) ? total : 0;
+}
+
+nyf_status nyf_filter_blf_batched(const float* f, const nyf_batch_item* items, int B, int n,
+                                  const nyf_params* p, float* out, void* ws, size_t ws_bytes,
+                                  void* stream) {
+  if (!f || !out) return NYF_ERR_INVALID_ARG;
+  return run_batched(items, B, n, p, ws, ws_bytes, stream,
+                     [&](int b, const nyf_params& q, void* wsb, size_t wsn, cudaStream_t s) {
+                       const nyf_batch_item& it = items[b];
+                       return blf_impl(f + it.offset, nullptr, it.H, it.W, n, n, &q, nullptr,
+                                       out + it.offset, wsb, wsn, s, false);
+                     });
+}
+
+nyf_status nyf_filter_blf_batched_backward(const float* f, const nyf_batch_item* items, int B,
+                                           int n, const nyf_params* p, const float* out,
+                                           const float* grad_out, float* grad_f,
+                                           float* grad_sigma, void* ws, size_t ws_bytes,
+                                           void* stream) {
+  if (!f || !out || !grad_out || !grad_f || !grad_sigma) return NYF_ERR_INVALID_ARG;
+  return run_batched(items, B, n, p, ws, ws_bytes, stream,
+                     [&](int b, const nyf_params& q, void* wsb, size_t wsn, cudaStream_t s) {
+                       const nyf_batch_item& it = items[b];
+                       return blf_backward_impl(f + it.offset, nullptr, it.H, it.W, n, n, &q,
+                                                out + it.offset, grad_out + it.offset,
+                                                grad_f + it.offset, nullptr, grad_sigma + 2 * b,
+                                                wsb, wsn, s, false);
+                     });
+}
+
+nyf_status nyf_batched_stats(const void* ws, const nyf_batch_item* items, int B, int n,
+                             const nyf_params* p, int b, nyf_stats* out, void* stream) {
+  if (!ws || !items || b < 0 || b >= B) return NYF_ERR_INVALID_ARG;
+  std::vector<size_t> offs(B);
+  size_t total = 0;
+  if (!batch_layout(items, B, n, p, offs.data(), &total)) return NYF_ERR_INVALID_ARG;
+  return nyf_get_stats(reinterpret_cast<const char*>(ws) + offs[b], out, stream);
 }
 
 }  // extern "C"

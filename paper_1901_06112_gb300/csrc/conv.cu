@@ -41,9 +41,8 @@ bool conv_split(int S, int n) {
 }
 
 cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void* phi, bool bf16,
-                                bool tensor_cores, int spatial, float sigma_s, int S,
-                                DevState* state, float* out, float* eta_out, float* zeta_ws,
-                                cudaStream_t st) {
+                                int tile, int spatial, float sigma_s, int S, DevState* state,
+                                float* out, float* eta_out, float* zeta_ws, cudaStream_t st) {
   const int Sc = conv_compiled_radius(S);
   if (Sc < 0) return cudaErrorInvalidValue;
   ConvArgs a;
@@ -63,7 +62,8 @@ cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void*
   for (int z = -S; z <= S; ++z) mass += a.box ? 1.0 : exp(-(double)z * z * a.inv2s2);
   a.eta_thr = (float)(1e-6 * mass * mass);
   // BF16 tensor-core kernel for S <= 16 when asked for; otherwise the FP32 FIR kernel
-  const bool mma = tensor_cores && S <= 16;
+  const bool mma = tile == NYF_TILE_TENSOR && S <= 16;
+  a.narrow = tile == NYF_TILE_NARROW ? 1 : 0;
   const bool split = mma ? conv_mma_split(n) : n + 1 > conv_nq(Sc);
   a.out = split ? nullptr : out;
   a.zeta = split ? zeta_ws : nullptr;

@@ -34,6 +34,7 @@ struct ConvArgs {
   float* out;               // H x W x n, when all quantities are in one CTA
   float* zeta;              // N x n, when they are split
   float* eta;               // N
+  int narrow;               // FP32 kernel: 32 x 64 tiles instead of 32 x 96 (S <= 16)
 };
 
 constexpr int kConvThreads = 256;
@@ -43,12 +44,12 @@ constexpr int kConvThreads = 256;
 // columns of one output row; NQ quantities per CTA, processed in pairs with
 // packed FP32x2 FMAs (one instruction, two planes).  Shared memory: NQ image
 // planes, two phi planes (double buffer) and the vertical-pass plane pair.
-template <int S>
+template <int S, bool WIDE = true>
 struct ConvCfg {
   static constexpr int TH = 32;
-  static constexpr int TW = S <= 16 ? 96 : (S <= 24 ? 48 : 64);
+  static constexpr int TW = S <= 16 ? (WIDE ? 96 : 64) : (S <= 24 ? 48 : 64);
   static constexpr int RV = 16;
-  static constexpr int RH = S <= 16 ? 12 : (S <= 24 ? 6 : 8);
+  static constexpr int RH = S <= 16 ? (WIDE ? 12 : 8) : (S <= 24 ? 6 : 8);
   static constexpr int NQ = S <= 24 ? 4 : 2;
   static constexpr int HH = TH + 2 * S;
   static constexpr int HW = TW + 2 * S;
@@ -76,9 +77,9 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Stage plane k of phi (tile + halo) into P: asynchronous for float32,
 // converted through registers for bfloat16.
-template <int S>
+template <int S, bool WIDE>
 __device__ __forceinline__ void stage_phi(const ConvArgs& a, float* P, int k, int ty0, int tx0) {
-  using C = ConvCfg<S>;
+  using C = ConvCfg<S, WIDE>;
   const int64_t base = (int64_t)k * a.N;
   if (!a.bf16) {
     const float* src = reinterpret_cast<const float*>(a.phi) + base;
@@ -103,9 +104,9 @@ __device__ __forceinline__ void stage_phi(const ConvArgs& a, float* P, int k, in
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-template <int S>
+template <int S, bool WIDE>
 __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
-  using C = ConvCfg<S>;
+  using C = ConvCfg<S, WIDE>;
   constexpr int T = 2 * S + 1;
   constexpr int TH = C::TH, TW = C::TW, RV = C::RV, RH = C::RH, NQ = C::NQ;
   constexpr int HH = C::HH, HW = C::HW, PS = C::PS, PLANE = C::PLANE;
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
     const bool in = c < n && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
     cp_async4(F + qi * PLANE + yy * PS + xx, in ? a.f + ((int64_t)gy * a.W + gx) * n + c : a.f, in);
   }
-  if (r > 0) stage_phi<S>(a, PB, 0, ty0, tx0);
+  if (r > 0) stage_phi<S, WIDE>(a, PB, 0, ty0, tx0);
   cp_async_commit();
 
   float2 g[T];
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
     // Prefetch phi_{k+1} into the other buffer while phi_k is consumed.  The
     // buffer was last read in iteration k-1, which ended with a barrier.
     if (k + 1 < r) {
-      stage_phi<S>(a, PB + ((k + 1) & 1) * PLANE, k + 1, ty0, tx0);
+      stage_phi<S, WIDE>(a, PB + ((k + 1) & 1) * PLANE, k + 1, ty0, tx0);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
@@ -256,12 +257,23 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
 
 template <int S>
 cudaError_t conv_launch(const ConvArgs& a, cudaStream_t st) {
-  using C = ConvCfg<S>;
-  cudaError_t e = cudaFuncSetAttribute(k_conv_combine<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)C::smem);
+  // the narrow tile exists for S <= 16 only; it is chosen by conv_tile == NYF_TILE_NARROW
+  if (S <= 16 && a.narrow) {
+    using C = ConvCfg<S, false>;
+    cudaError_t e = cudaFuncSetAttribute(k_conv_combine<S, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.W + C::TW - 1) / C::TW, (a.H + C::TH - 1) / C::TH, (a.n + 1 + C::NQ - 1) / C::NQ);
+    k_conv_combine<S, false><<<grid, kConvThreads, C::smem, st>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  using C = ConvCfg<S, true>;
+  cudaError_t e = cudaFuncSetAttribute(k_conv_combine<S, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
   if (e != cudaSuccess) return e;
   dim3 grid((a.W + C::TW - 1) / C::TW, (a.H + C::TH - 1) / C::TH, (a.n + 1 + C::NQ - 1) / C::NQ);
-  k_conv_combine<S><<<grid, kConvThreads, C::smem, st>>>(a);
+  k_conv_combine<S, true><<<grid, kConvThreads, C::smem, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -90,9 +90,8 @@ cudaError_t launch_features_nlm(const float* f, int H, int W, int n, int r, cons
                                 void* phi, bool bf16, cudaStream_t st);
 size_t features_nlm_smem_bytes(int K, int n, int r);
 cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void* phi, bool bf16,
-                                bool tensor_cores, int spatial, float sigma_s, int S,
-                                DevState* state, float* out, float* eta_out, float* zeta_ws,
-                                cudaStream_t st);
+                                int tile, int spatial, float sigma_s, int S, DevState* state,
+                                float* out, float* eta_out, float* zeta_ws, cudaStream_t st);
 int conv_compiled_radius(int S);
 bool conv_split(int S, int n);
 cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spatial, float sigma_s,

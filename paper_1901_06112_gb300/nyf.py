@@ -31,6 +31,7 @@ class Params:
     S: int = 0                     # window radius; 0 -> ceil(3 sigma_s)
     patch_radius: int = 0          # NLM patch radius
     sample_frac: float = 1.0
+    conv_tile: str = "auto"        # "auto" | "wide" | "narrow" | "tensor"
 
     def c(self) -> L.NyfParams:
         return L.NyfParams(float(self.sigma_s), float(self.sigma_r), int(self.K),
@@ -38,7 +39,9 @@ class Params:
                            float(self.eig_rel_tol),
                            L.BF16 if self.precision == "bf16" else L.FP32,
                            L.BOX if self.spatial == "box" else L.GAUSSIAN, int(self.S),
-                           int(self.patch_radius), float(self.sample_frac))
+                           int(self.patch_radius), float(self.sample_frac),
+                           {"auto": L.TILE_AUTO, "wide": L.TILE_WIDE, "narrow": L.TILE_NARROW,
+                            "tensor": L.TILE_TENSOR}[self.conv_tile])
 
     @property
     def radius(self) -> int:
@@ -255,3 +258,98 @@ class NyfBLF(torch.autograd.Function):
 def blf_autograd(f, sigma_r, sigma_s, params: Params, guide=None, landmarks=None):
     """g_hat with autograd support; sigma_r / sigma_s may be 0-dim tensors."""
     return NyfBLF.apply(f, guide, sigma_r, sigma_s, params, landmarks)
+
+
+# ----------------------------------------------------------------------------- batched
+
+class Batched:
+    """A batch of colour images of uneven sizes filtered by one call per pass.
+
+    The images live packed (HWC, back to back) in one device buffer; image b
+    has its own sigma_s, sigma_r (and optionally a tuned convolution variant).
+    forward()/backward() enqueue the whole batch; capture() records one
+    forward + backward into a CUDA graph that replay() launches again.
+    """
+
+    TILES = {"auto": L.TILE_AUTO, "wide": L.TILE_WIDE, "narrow": L.TILE_NARROW,
+             "tensor": L.TILE_TENSOR}
+
+    def __init__(self, shapes, sigmas_s, sigmas_r, params: Params, n=3, device="cuda",
+                 tiles=None):
+        self.lib = L.load()
+        self.B = len(shapes)
+        self.n = n
+        self.params = params
+        self.items = (L.NyfBatchItem * self.B)()
+        off = 0
+        self.offsets = []
+        for b, (H, W) in enumerate(shapes):
+            t = self.TILES[tiles[b]] if tiles else L.TILE_AUTO
+            self.items[b] = L.NyfBatchItem(off, int(H), int(W), float(sigmas_s[b]),
+                                           float(sigmas_r[b]), t, 0)
+            self.offsets.append(off)
+            off += int(H) * int(W) * n
+        self.total = off
+        self.shapes = [(int(H), int(W)) for H, W in shapes]
+        self._p = params.c()
+        nbytes = self.lib.nyf_batched_workspace_size(self.items, self.B, n, C.byref(self._p))
+        if nbytes == 0:
+            raise ValueError("invalid batch for nyf_batched_workspace_size")
+        self.ws = Workspace(nbytes, device)
+        self.grad_sigma = torch.zeros((self.B, 2), dtype=torch.float32, device=device)
+        self.graph = None
+
+    def pack(self, images):
+        return torch.cat([torch.as_tensor(im).reshape(-1) for im in images]).to(
+            self.ws.buf.device, torch.float32).contiguous()
+
+    def unpack(self, flat):
+        out = []
+        for (H, W), o in zip(self.shapes, self.offsets):
+            out.append(flat[o:o + H * W * self.n].view(H, W, self.n))
+        return out
+
+    def forward(self, f, out=None):
+        out = torch.empty_like(f) if out is None else out
+        L.check(self.lib.nyf_filter_blf_batched(_ptr(f), self.items, self.B, self.n,
+                                                C.byref(self._p), _ptr(out), self.ws.cptr(),
+                                                self.ws.nbytes, _stream()),
+                "nyf_filter_blf_batched")
+        return out
+
+    def backward(self, f, out, grad_out, grad_f=None):
+        grad_f = torch.empty_like(f) if grad_f is None else grad_f
+        L.check(self.lib.nyf_filter_blf_batched_backward(
+            _ptr(f), self.items, self.B, self.n, C.byref(self._p), _ptr(out), _ptr(grad_out),
+            _ptr(grad_f), _ptr(self.grad_sigma), self.ws.cptr(), self.ws.nbytes, _stream()),
+            "nyf_filter_blf_batched_backward")
+        return grad_f, self.grad_sigma
+
+    def stats(self, b):
+        s = L.NyfStats()
+        L.check(self.lib.nyf_batched_stats(self.ws.cptr(), self.items, self.B, self.n,
+                                           C.byref(self._p), b, C.byref(s), _stream()),
+                "nyf_batched_stats")
+        return {k: getattr(s, k) for k, _ in L.NyfStats._fields_}
+
+    def capture(self, f, grad_out):
+        """Record forward + backward on static buffers into a CUDA graph."""
+        self.f_static, self.g_static = f, grad_out
+        self.out_static = torch.empty_like(f)
+        self.gf_static = torch.empty_like(f)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):                # warm-up outside the graph
+            self.forward(f, self.out_static)
+            self.backward(f, self.out_static, grad_out, self.gf_static)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.forward(self.f_static, self.out_static)
+            self.backward(self.f_static, self.out_static, self.g_static, self.gf_static)
+        return self.out_static, self.gf_static, self.grad_sigma
+
+    def replay(self):
+        self.graph.replay()
+        return self.out_static, self.gf_static, self.grad_sigma

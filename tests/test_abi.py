@@ -28,12 +28,12 @@ def test_status_strings_and_version(lib):
 
 
 def test_workspace_size_host_logic(lib):
-    p = _lib.NyfParams(3.0, 30.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0)
+    p = _lib.NyfParams(3.0, 30.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0, 0)
     s1 = lib.nyf_workspace_size(256, 256, 3, 3, C.byref(p))
     s2 = lib.nyf_workspace_size(512, 256, 3, 3, C.byref(p))
     assert s1 > 0 and s2 > s1
-    p.precision = 1
-    assert lib.nyf_workspace_size(256, 256, 3, 3, C.byref(p)) < s1     # bf16 features are smaller
+    p.precision = 1                 # the filters keep their features in float32 either way
+    assert lib.nyf_workspace_size(256, 256, 3, 3, C.byref(p)) == s1
     p.K = 0
     assert lib.nyf_workspace_size(256, 256, 3, 3, C.byref(p)) == 0
     p.K = 8
@@ -42,18 +42,18 @@ def test_workspace_size_host_logic(lib):
 
 
 def test_argument_errors_return_before_any_launch(lib):
-    p = _lib.NyfParams(3.0, 30.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0)
+    p = _lib.NyfParams(3.0, 30.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0, 0)
     bad = C.c_void_p(256)
     # null image
     assert lib.nyf_filter_blf(None, None, 8, 8, 3, 3, C.byref(p), None, bad, bad, 1 << 20, None) == 1
     # negative sigma_r
-    q = _lib.NyfParams(3.0, -1.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0)
+    q = _lib.NyfParams(3.0, -1.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0, 0)
     assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(q), None, bad, bad, 1 << 20, None) == 1
     # too many landmarks
-    q = _lib.NyfParams(3.0, 30.0, 65, 10, 0, 1e-7, 0, 0, 0, 0, 1.0)
+    q = _lib.NyfParams(3.0, 30.0, 65, 10, 0, 1e-7, 0, 0, 0, 0, 1.0, 0)
     assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(q), None, bad, bad, 1 << 20, None) == 1
     # window radius beyond the compiled maximum
-    q = _lib.NyfParams(11.0, 30.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0)
+    q = _lib.NyfParams(11.0, 30.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0, 0)
     assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(q), None, bad, bad, 1 << 20, None) == 2
     # workspace too small / misaligned
     assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(p), None, bad, bad, 16, None) == 3
@@ -63,3 +63,18 @@ def test_argument_errors_return_before_any_launch(lib):
     assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 2, C.byref(p), None, bad, bad, 1 << 30, None) == 1
     # k-means: more clusters than rows
     assert lib.nyf_kmeans(bad, 4, 3, 8, 1, 0, None, bad, None, None, bad, 1 << 20, None) == 1
+
+
+def test_batched_workspace_is_the_sum_of_aligned_slices(lib):
+    p = _lib.NyfParams(3.0, 30.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0, 0)
+    items = (_lib.NyfBatchItem * 3)(_lib.NyfBatchItem(0, 64, 80, 2.0, 30.0, 0, 0),
+                                    _lib.NyfBatchItem(64 * 80 * 3, 1, 57, 1.0, 20.0, 0, 0),
+                                    _lib.NyfBatchItem(64 * 80 * 3 + 57 * 3, 33, 7, 3.0, 50.0, 0, 0))
+    total = lib.nyf_batched_workspace_size(items, 3, 3, C.byref(p))
+    want = 0
+    for it in items:
+        q = _lib.NyfParams(it.sigma_s, it.sigma_r, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0, 0)
+        want = (want + lib.nyf_workspace_size(it.H, it.W, 3, 3, C.byref(q)) + 255) // 256 * 256
+    assert total == want
+    items[1].H = 0
+    assert lib.nyf_batched_workspace_size(items, 3, 3, C.byref(p)) == 0
