@@ -42,7 +42,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
-    ap.add_argument("--mode", default="fwd", choices=["fwd", "fwdbwd"])
+    ap.add_argument("--mode", default="fwdbwd", choices=["fwd", "fwdbwd"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the forward-only, BF16 and batched side measurements")
     ap.add_argument("--impl", default="nyf", choices=["nyf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -51,40 +53,45 @@ def parse():
 
 # ----------------------------------------------------------------------------- CPU oracle leg
 
-CPU_SAMPLE = (384, 384)     # crop of the workload the oracle filters per step
+CPU_SAMPLE = (192, 192)     # crop of the workload the oracle filters (and differentiates) per step
 
 
-def _oracle_step_code(h, w):
+def _oracle_step_code(h, w, backward):
     return f"""
 import os, sys, time, json
 sys.path.insert(0, {ROOT!r})
 import numpy as np
 from paper_1901_06112_gb300 import synth
-from oracle import pipeline as pl
+from oracle import pipeline as pl, grad as gr
 wl = synth.colour_blf_hd()
 f = wl.f[:{h}, :{w}].astype(np.float64)
 t0 = time.perf_counter()
 g, mu, info = pl.blf(f, wl.sigma_s, wl.sigma_r, wl.K, iters=wl.kmeans_iters, seed=wl.seed)
+if {backward!r}:
+    G = np.random.default_rng(0).normal(size=f.shape)
+    gr.vjp(f, f, mu, wl.sigma_r, wl.sigma_s, wl.radius, 1e-7, G, guide_is_image=True)
 dt = time.perf_counter() - t0
 print(json.dumps({{"seconds": dt, "pixels": {h * w}}}))
 """
 
 
-def cpu_oracle_seconds(h=CPU_SAMPLE[0], w=CPU_SAMPLE[1]):
-    """Time the FP64 oracle (k-means + Algorithm 1) on an h x w crop, one thread."""
+def cpu_oracle_seconds(h=CPU_SAMPLE[0], w=CPU_SAMPLE[1], backward=True):
+    """Time the FP64 oracle (k-means + Algorithm 1, and its gradient) on an h x w crop."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", _oracle_step_code(h, w)], capture_output=True,
-                       text=True, env=env, timeout=900)
+    r = subprocess.run([sys.executable, "-c", _oracle_step_code(h, w, backward)],
+                       capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
     return d["seconds"], d["pixels"]
 
 
-def cpu_baseline_obj():
-    sec, px = cpu_oracle_seconds()
+def cpu_baseline_obj(backward=True):
+    sec, px = cpu_oracle_seconds(backward=backward)
+    what = "forward + backward" if backward else "forward"
     return {"value": px / 1e6 / sec, "unit": "megapixels/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle (k-means 10 iters + Algorithm 1) on a {CPU_SAMPLE[0]}x"
+            "sample": f"FP64 oracle {what} (k-means 10 iters + Algorithm 1"
+                      f"{' + autograd gradient' if backward else ''}) on a {CPU_SAMPLE[0]}x"
                       f"{CPU_SAMPLE[1]} crop of the workload, one thread, {sec:.1f} s"}
 
 
@@ -96,10 +103,11 @@ def run_reference(args):
     times = []
     px = 0
     for _ in range(max(0, min(args.warmup, 1))):
-        cpu_oracle_seconds(128, 128)
-    # each step is a bounded sample of the workload (a 256 x 256 crop)
+        cpu_oracle_seconds(64, 64, backward=args.mode == "fwdbwd")
+    # each step is a bounded sample of the workload (a crop, forward + backward)
+    bwd = args.mode == "fwdbwd"
     for _ in range(min(steps, 3)):
-        sec, px = cpu_oracle_seconds(256, 256)
+        sec, px = cpu_oracle_seconds(backward=bwd)
         times.append(sec)
     sec = float(np.median(times))
     v = px / 1e6 / sec
@@ -107,10 +115,12 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": len(times), "warmup": args.warmup,
             "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "colour_blf_1920x1080_K32 (256x256 crop per step)",
-                       "sigma_s": 5.0, "sigma_r": 40.0, "K": 32, "mode": "fwd"},
+            "config": {"workload": f"colour_blf_1920x1080_K32 ({CPU_SAMPLE[0]}x{CPU_SAMPLE[1]} "
+                                   "crop per step)",
+                       "sigma_s": 5.0, "sigma_r": 40.0, "K": 32, "mode": args.mode},
             "cpu_baseline": {"value": v, "unit": "megapixels/s", "cores": 1, "kind": "oracle",
-                             "sample": "256x256 crop of the 1920x1080 workload per step"},
+                             "sample": f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]} crop of the 1920x1080 "
+                                       "workload per step, FP64 oracle, one thread"},
             "e2e": {"value": v, "unit": "megapixels/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -174,12 +184,79 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- GPU leg
 
 def conv_flops_per_pixel(K, n, S):
-    """Algorithmic FLOPs of the convolution + combine stage per pixel.
+    """Algorithmic FLOPs of the forward convolution + combine per pixel.
 
     K (n + 1) planes, each a separable FIR of 2 passes x (2S + 1) taps x 2 FLOP,
     plus the combine multiply-add of every plane.
     """
     return K * (n + 1) * (2 * (2 * S + 1) * 2 + 2)
+
+
+def conv_bwd_flops_per_pixel(K, n, S):
+    """Algorithmic FLOPs of the adjoint convolutions per pixel.
+
+    Per plane: omega * (phi f), omega * (a phi) (2 passes each) and the sigma_s
+    term (g' (x) g + g (x) g') * (phi f) sharing the vertical g pass (3 more
+    passes): 7 passes x (2S + 1) taps x 2 FLOP, plus 6 FLOP of products.
+    """
+    return K * (n + 1) * (7 * (2 * S + 1) * 2 + 6)
+
+
+STAGES = ["landmarks", "eig", "features", "conv_combine", "bwd_conv", "bwd_features"]
+
+
+def timed_steps(step, steps, flush, stream, lib):
+    """Per-step CUDA-event times (ms) and per-stage library event times."""
+    import ctypes as C
+    import torch
+    buf = (C.c_float * 7)()
+    step_ms, stage_ms = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        lib.nyf_get_timing(buf, 7)
+        stage_ms.append([buf[i] for i in range(7)])
+    st = np.array(stage_ms)
+    means = [float(np.mean(st[:, i][st[:, i] >= 0])) if np.any(st[:, i] >= 0) else None
+             for i in range(7)]
+    return float(np.mean(step_ms)), means
+
+
+def batched_extra(nyf, steps, warmup, flush, stream):
+    """The 64-image workload (BF16, K = 16): forward + backward by CUDA-graph replay."""
+    import torch
+    from paper_1901_06112_gb300 import synth
+    batch = synth.batched_blf()
+    shapes = [(w.H, w.W) for w in batch]
+    P = nyf.Params(K=16, kmeans_iters=10, precision="bf16")
+    bt = nyf.Batched(shapes, [w.sigma_s for w in batch], [w.sigma_r for w in batch], P)
+    f = bt.pack([w.f for w in batch])
+    G = torch.randn(f.shape, generator=torch.Generator().manual_seed(0)).cuda()
+    bt.capture(f, G)
+    for _ in range(warmup):
+        bt.replay()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.replay()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    mpix = bt.total / 3 / 1e6
+    t = float(np.mean(ms))
+    return {"workload": "batched_blf_64_images_128-1024_K16_bf16", "images": len(batch),
+            "megapixels": mpix, "ms_per_step": t, "value": mpix / (t / 1e3),
+            "unit": "megapixels/s", "mode": "fwd+bwd, one CUDA-graph replay per step"}
 
 
 def main():
@@ -205,22 +282,29 @@ def main():
     lib = _lib.load()
     wl = synth.colour_blf_hd()
     H, W, n = wl.f.shape
-    P = nyf.Params(sigma_s=wl.sigma_s, sigma_r=wl.sigma_r, K=wl.K, kmeans_iters=wl.kmeans_iters,
-                   seed=wl.seed + rank, precision=args.precision)
+    fwdbwd = args.mode == "fwdbwd"
+
+    def make(precision):
+        return nyf.Params(sigma_s=wl.sigma_s, sigma_r=wl.sigma_r, K=wl.K,
+                          kmeans_iters=wl.kmeans_iters, seed=wl.seed + rank, precision=precision)
+
+    P = make(args.precision)
     f_dev = torch.from_numpy(wl.f).to(dev)
     out = torch.empty_like(f_dev)
     ws = nyf.make_workspace(H, W, n, n, P, dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
-    fwdbwd = args.mode == "fwdbwd"
-    if fwdbwd:
-        G = torch.randn_like(f_dev)
-        grads = nyf.BackwardBuffers(f_dev)
+    G = torch.randn(f_dev.shape, generator=torch.Generator().manual_seed(0)).to(dev)
+    grads = nyf.BackwardBuffers(f_dev)
+    stream = torch.cuda.current_stream()
 
-    def step():
-        nyf.blf(f_dev, P, out=out, ws=ws)
-        if fwdbwd:
-            nyf.blf_backward(f_dev, P, out, G, ws, grads)
+    def make_step(Pp, bwd):
+        def step():
+            nyf.blf(f_dev, Pp, out=out, ws=ws)
+            if bwd:
+                nyf.blf_backward(f_dev, Pp, out, G, ws, grads)
+        return step
 
+    step = make_step(P, fwdbwd)
     lib.nyf_set_timing(1)
     for _ in range(max(3, args.warmup)):
         step()
@@ -232,31 +316,16 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     launches0 = lib.nyf_launch_count()
-    step_ms, stage_ms = [], []
-    import ctypes as C
-    buf = (C.c_float * 7)()
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        lib.nyf_get_timing(buf, 7)
-        stage_ms.append([buf[i] for i in range(7)])
+    ms, stage_mean = timed_steps(step, args.steps, flush, stream, lib)
     torch.cuda.synchronize()
     launches = lib.nyf_launch_count() - launches0
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    ms = float(np.mean(step_ms))
     t = torch.tensor([ms], device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -264,14 +333,42 @@ def main():
     mp = H * W / 1e6
     value = world * mp / (ms_max / 1e3)
 
-    stage = np.array(stage_ms)
-    stage_mean = [float(np.mean(stage[:, i][stage[:, i] >= 0])) if np.any(stage[:, i] >= 0) else None
-                  for i in range(7)]
     r = st["rank"]
-    flops = conv_flops_per_pixel(r, n, P.radius) * H * W
-    conv_ms = stage_mean[3]
+    planes = wl.K if r > 0 else 0
     peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = flops / (conv_ms / 1e3) / 1e12
+    fwd_flops = conv_flops_per_pixel(planes, n, P.radius) * H * W
+    bwd_flops = conv_bwd_flops_per_pixel(planes, n, P.radius) * H * W
+
+    def roof(name, flops, ms_k):
+        a = flops / (ms_k / 1e3) / 1e12
+        return {"kernel": name, "bound": "alu" if args.precision == "fp32" or name != "conv_combine"
+                else "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                "traffic": None, "launch_ms": ms_k,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FP32 ALU)"}
+
+    roof_fwd = roof("conv_combine", fwd_flops, stage_mean[3])
+    roof_bwd = roof("conv_bwd", bwd_flops, stage_mean[4]) if fwdbwd else None
+    dominant = roof_bwd if (fwdbwd and stage_mean[4] > stage_mean[3]) else roof_fwd
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        lib.nyf_set_timing(0)
+        if fwdbwd:
+            fwd_ms, _ = timed_steps(make_step(P, False), max(3, args.steps // 2), flush, stream, lib)
+            extras["fwd"] = {"value": mp / (fwd_ms / 1e3), "ms_per_step": fwd_ms,
+                             "unit": "megapixels/s", "precision": args.precision}
+        other = "bf16" if args.precision == "fp32" else "fp32"
+        Po = make(other)
+        for _ in range(2):
+            make_step(Po, fwdbwd)()
+        o_ms, _ = timed_steps(make_step(Po, fwdbwd), max(3, args.steps // 2), flush, stream, lib)
+        f_ms, _ = timed_steps(make_step(Po, False), max(3, args.steps // 2), flush, stream, lib)
+        extras[other] = {"fwdbwd_value" if fwdbwd else "value": mp / (o_ms / 1e3),
+                         "fwd_value": mp / (f_ms / 1e3), "unit": "megapixels/s"}
+        try:
+            extras["batched"] = batched_extra(nyf, max(3, args.steps // 4), 2, flush, stream)
+        except Exception as ex:                   # the side measurement must not hide the main one
+            extras["batched"] = {"error": str(ex)[:300]}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -286,9 +383,7 @@ def main():
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             f_dev.copy_(f_host, non_blocking=True)
-            nyf.blf(f_dev, P, out=out, ws=ws)
-            if fwdbwd:
-                nyf.blf_backward(f_dev, P, out, G, ws, grads)
+            step()
             o_host.copy_(out, non_blocking=True)
             e1.record(stream)
             e1.synchronize()
@@ -306,28 +401,25 @@ def main():
             "metric": METRIC, "value": value, "unit": "megapixels/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
+            "dtype": "f32" if args.precision == "fp32" else "bf16",
             "data": "synthetic",
             "config": {"workload": wl.name, "H": H, "W": W, "n": n, "sigma_s": wl.sigma_s,
                        "sigma_r": wl.sigma_r, "K": wl.K, "kmeans_iters": wl.kmeans_iters,
-                       "precision": args.precision, "mode": args.mode, "rank_r": r,
+                       "precision": args.precision,
+                       "mode": "fwd+bwd" if fwdbwd else "fwd", "rank_r": r,
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{world}"},
-            "stages_ms": {"landmarks": stage_mean[0], "eig": stage_mean[1],
-                          "features": stage_mean[2], "conv_combine": stage_mean[3],
-                          "bwd_conv": stage_mean[4], "bwd_features": stage_mean[5],
-                          "bwd_tail": stage_mean[6]},
-            "roofline": {"kernel": "conv_combine", "bound": "alu", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": None,
-                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"},
+            "stages_ms": dict(zip(STAGES, stage_mean[:6])),
+            "roofline": dominant,
+            "roofline_conv_fwd": roof_fwd,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk,
+            "extras": extras,
         }
-        if not args.no_cpu_baseline and world >= 1 and rank == 0 and world == 1:
+        if not args.no_cpu_baseline and world == 1:
             try:
-                line["cpu_baseline"] = cpu_baseline_obj()
+                line["cpu_baseline"] = cpu_baseline_obj(backward=fwdbwd)
             except Exception as ex:  # the oracle leg must not hide the GPU number
                 line["cpu_baseline"] = {"error": str(ex)[:200]}
         print(json.dumps(line), flush=True)
