@@ -2,8 +2,8 @@
 // Eqs. (9)-(12)), and the host launcher of the whole backward pass.
 //
 // With E_im = exp(-D_im / (2 sigma_r^2)), D_im = ||p_i - mu_m||^2 and
-// Phi = E W_hat (W_hat = W_r Lambda_r^{-1/2}, so W_hat W_hat^T is the truncated
-// inverse of A):
+// Phi = E W_hat (W_hat = W_r Lambda_r^{-1/2} W_r^T, the symmetric factor, so
+// W_hat W_hat^T is the truncated inverse of A):
 //   dE_im = sum_k dPhi_ik W_hat[m][k]
 //   dp_i  = sum_m (-E_im dE_im / (2 sigma_r^2)) 2 (p_i - mu_m)
 //   dsigma_r (through E) = sum_im dE_im E_im D_im / sigma_r^3
@@ -20,7 +20,7 @@
 namespace nyf {
 namespace {
 
-constexpr int kFbBlocks = 304;      // features-backward CTAs (2 per SM)
+constexpr int kFbBlocks = 456;      // features-backward CTAs (3 per SM)
 constexpr int kFbThreads = 256;
 
 __host__ __device__ inline int kpad4(int K) { return (K + 3) & ~3; }
@@ -58,100 +58,94 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
     const int64_t i = base + tid;
     const bool valid = i < N;
     const float* p = guide + (valid ? i : 0) * rho;
-    float x[RB > 0 ? RB : 1];
-    if (RB > 0) {
+    constexpr int RX = RB > 0 ? RB : 1;
+    float x[RX], dp[RX];
 #pragma unroll
-      for (int d = 0; d < (RB > 0 ? RB : 1); ++d) x[d] = (d < rho) ? __ldg(p + d) : 0.f;
+    for (int d = 0; d < RX; ++d) {
+      x[d] = (RB > 0 && d < rho) ? __ldg(p + d) : 0.f;
+      dp[d] = 0.f;
     }
-    float e[KB], d2[KB], g[KB];
-#pragma unroll
-    for (int m = 0; m < KB; ++m) {
-      float s = 0.f;
-      if (m < K) {
-        const float* c = mu + m * rho;
-        if (RB > 0) {
-#pragma unroll
-          for (int d = 0; d < (RB > 0 ? RB : 1); ++d)
-            if (d < rho) {
-              const float t = x[d] - c[d];
-              s = fmaf(t, t, s);
-            }
-        } else {
-          for (int d = 0; d < rho; ++d) {
-            const float t = __ldg(p + d) - c[d];
-            s = fmaf(t, t, s);
-          }
-        }
-      }
-      d2[m] = s;
-      e[m] = (m < K && valid) ? expf(-s * inv2s2r) : 0.f;
-    }
+    float g[KB];                                   // dPhi of this pixel
 #pragma unroll
     for (int k = 0; k < KB; ++k) g[k] = (valid && k < r) ? dphi[(int64_t)k * N + i] : 0.f;
-    // dE_m = sum_k dPhi_k W_hat[m][k]; dD_m; sigma_r and guide terms
-    float dD[KB];
+    // one landmark at a time: E_m, dE_m = sum_k dPhi_k W_hat[m][k], then its terms
+    for (int m = 0; m < K; ++m) {
+      const float* c = mu + m * rho;
+      float d2 = 0.f;
+      if (RB > 0) {
 #pragma unroll
-    for (int m = 0; m < KB; ++m) {
-      float de = 0.f;
-      if (m < K) {
-#pragma unroll
-        for (int k = 0; k < KB; k += 4) {
-          if (k < r) {
-            const float4 w = *reinterpret_cast<const float4*>(Wsm + m * KP + k);
-            de = fmaf(g[k], w.x, de);
-            if (k + 1 < KB) de = fmaf(g[k + 1 < KB ? k + 1 : k], w.y, de);
-            if (k + 2 < KB) de = fmaf(g[k + 2 < KB ? k + 2 : k], w.z, de);
-            if (k + 3 < KB) de = fmaf(g[k + 3 < KB ? k + 3 : k], w.w, de);
+        for (int d = 0; d < RX; ++d)
+          if (d < rho) {
+            const float t = x[d] - c[d];
+            d2 = fmaf(t, t, d2);
           }
+      } else {
+        for (int d = 0; d < rho; ++d) {
+          const float t = __ldg(p + d) - c[d];
+          d2 = fmaf(t, t, d2);
         }
       }
-      srp = fmaf(de * e[m], d2[m], srp);
-      dD[m] = -e[m] * de * inv2s2r;
-    }
-    if (valid) {
-      float* dst = dguide + i * rho;
-      for (int d = 0; d < rho; ++d) {
-        const float xd = RB > 0 ? 0.f : __ldg(p + d);
-        float s = 0.f;
+      const float e = valid ? expf(-d2 * inv2s2r) : 0.f;
+      float de0 = 0.f, de1 = 0.f;
 #pragma unroll
-        for (int m = 0; m < KB; ++m)
-          if (m < K) {
-            float xv = xd;
-            if (RB > 0) {
-#pragma unroll
-              for (int q = 0; q < (RB > 0 ? RB : 1); ++q) if (q == d) xv = x[q];
-            }
-            s = fmaf(dD[m], 2.f * (xv - mu[m * rho + d]), s);
-          }
-        dst[d] = add_into ? dst[d] + s : s;
+      for (int k = 0; k < KB; k += 4) {
+        if (k < r) {
+          const float4 w = *reinterpret_cast<const float4*>(Wsm + m * KP + k);
+          de0 = fmaf(g[k], w.x, de0);
+          de1 = fmaf(g[k + 1], w.y, de1);
+          de0 = fmaf(g[k + 2], w.z, de0);
+          de1 = fmaf(g[k + 3], w.w, de1);
+        }
       }
+      const float de = de0 + de1;
+      srp = fmaf(de * e, d2, srp);
+      const float dDm = -e * de * inv2s2r;
+      if (RB > 0) {
+#pragma unroll
+        for (int d = 0; d < RX; ++d)
+          if (d < rho) dp[d] = fmaf(dDm, 2.f * (x[d] - c[d]), dp[d]);
+      } else if (valid) {
+        float* dst = dguide + i * rho;
+        for (int d = 0; d < rho; ++d) {
+          const float v = dDm * 2.f * (__ldg(p + d) - c[d]);
+          dst[d] = (m == 0 && !add_into) ? v : dst[d] + v;
+        }
+      }
+      Es[tid * KB + m] = e;
+    }
+    for (int m = K; m < KB; ++m) Es[tid * KB + m] = 0.f;
+    if (RB > 0 && valid) {
+      float* dst = dguide + i * rho;
+#pragma unroll
+      for (int d = 0; d < RX; ++d)
+        if (d < rho) dst[d] = add_into ? dst[d] + dp[d] : dp[d];
     }
 #pragma unroll
-    for (int m = 0; m < KB; ++m) {
-      Es[tid * KB + m] = e[m];
-      Ds[tid * KB + m] = g[m];
-    }
+    for (int k = 0; k < KB; ++k) Ds[tid * KB + k] = g[k];
     __syncthreads();
-    // G_W += E^T dPhi over this round's pixels
+    // G_W += E^T dPhi over this round's pixels (four independent partial sums)
     const int nb = (K + 1) / 2, rb = (r + 1) / 2;
 #pragma unroll
     for (int o = 0; o < kMaxOwn; ++o) {
       const int blk = tid + o * kFbThreads;
       if (blk < nb * rb) {
         const int m0 = 2 * (blk / rb), k0 = 2 * (blk % rb);
-        float s0 = gw[o][0], s1 = gw[o][1], s2 = gw[o][2], s3 = gw[o][3];
-        for (int px = 0; px < kFbThreads; ++px) {
-          const float2 ev = *reinterpret_cast<const float2*>(Es + px * KB + m0);
-          const float2 dv = *reinterpret_cast<const float2*>(Ds + px * KB + k0);
-          s0 = fmaf(ev.x, dv.x, s0);
-          s1 = fmaf(ev.x, dv.y, s1);
-          s2 = fmaf(ev.y, dv.x, s2);
-          s3 = fmaf(ev.y, dv.y, s3);
+        float s[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u][0] = s[u][1] = s[u][2] = s[u][3] = 0.f;
+        for (int px = 0; px < kFbThreads; px += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float2 ev = *reinterpret_cast<const float2*>(Es + (px + u) * KB + m0);
+            const float2 dv = *reinterpret_cast<const float2*>(Ds + (px + u) * KB + k0);
+            s[u][0] = fmaf(ev.x, dv.x, s[u][0]);
+            s[u][1] = fmaf(ev.x, dv.y, s[u][1]);
+            s[u][2] = fmaf(ev.y, dv.x, s[u][2]);
+            s[u][3] = fmaf(ev.y, dv.y, s[u][3]);
+          }
         }
-        gw[o][0] = s0;
-        gw[o][1] = s1;
-        gw[o][2] = s2;
-        gw[o][3] = s3;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gw[o][q] += (s[0][q] + s[1][q]) + (s[2][q] + s[3][q]);
       }
     }
     __syncthreads();

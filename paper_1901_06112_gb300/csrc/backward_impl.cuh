@@ -140,14 +140,15 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
     Aq[qi * PLANE + yy * PS + xx] = v;
   }
 
-  float g[T], gp[T];
+  // (g, g') tap pairs: one packed FMA updates the g and g' accumulators of an input
+  float2 gg[T];
 #pragma unroll
   for (int t = 0; t < T; ++t) {
     const int z = t - S;
     const float zz = (float)(z * z);
     const bool on = !(z > a.S_true || -z > a.S_true);
-    g[t] = on ? (a.box ? 1.f : expf(-zz * a.inv2s2)) : 0.f;
-    gp[t] = (on && !a.box) ? g[t] * zz * a.inv_s3 : 0.f;
+    const float gv = on ? (a.box ? 1.f : expf(-zz * a.inv2s2)) : 0.f;
+    gg[t] = make_float2(gv, (on && !a.box) ? gv * zz * a.inv_s3 : 0.f);
   }
 
   float dfa[NQ][RH];
@@ -182,48 +183,56 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
         const float* Aqq = Aq + qi * PLANE;
         for (int task = tid; task < C::VT; task += kConvThreads) {
           const int vx = task % HW, vy0 = (task / HW) * RV;
-          float va[RV], vp[RV], vb[RV];
+          float2 vap[RV];            // (g, g') on phi f
+          float vb[RV];              // g on a phi
 #pragma unroll
-          for (int j = 0; j < RV; ++j) va[j] = vp[j] = vb[j] = 0.f;
+          for (int j = 0; j < RV; ++j) {
+            vap[j] = make_float2(0.f, 0.f);
+            vb[j] = 0.f;
+          }
 #pragma unroll
           for (int i = 0; i < RV + 2 * S; ++i) {
             const int off = (vy0 + i) * PS + vx;
             const float p = P[off];
             const float h = den ? p : p * Fq[off];
             const float u = p * Aqq[off];
+            const float2 hh = make_float2(h, h);
 #pragma unroll
             for (int j = 0; j < RV; ++j) {
               const int t = i - j;
               if (t >= 0 && t < T) {
-                va[j] = fmaf(g[t], h, va[j]);
-                vp[j] = fmaf(gp[t], h, vp[j]);
-                vb[j] = fmaf(g[t], u, vb[j]);
+                vap[j] = __ffma2_rn(gg[t], hh, vap[j]);
+                vb[j] = fmaf(gg[t].x, u, vb[j]);
               }
             }
           }
 #pragma unroll
           for (int j = 0; j < RV; ++j) {
-            Mg[(vy0 + j) * PS + vx] = va[j];
-            Mp[(vy0 + j) * PS + vx] = vp[j];
+            Mg[(vy0 + j) * PS + vx] = vap[j].x;
+            Mp[(vy0 + j) * PS + vx] = vap[j].y;
             Mb[(vy0 + j) * PS + vx] = vb[j];
           }
         }
         __syncthreads();
-        float cc[RH], cp[RH], bb[RH];
+        float2 ccp[RH];              // (g on Mg, g' on Mg + g on Mp)
+        float bb[RH];
 #pragma unroll
-        for (int j = 0; j < RH; ++j) cc[j] = cp[j] = bb[j] = 0.f;
+        for (int j = 0; j < RH; ++j) {
+          ccp[j] = make_float2(0.f, 0.f);
+          bb[j] = 0.f;
+        }
 #pragma unroll
         for (int i = 0; i < RH + 2 * S; ++i) {
           const int off = hy * PS + hx0 + i;
           const float mg = Mg[off], mp = Mp[off], mb = Mb[off];
+          const float2 mm = make_float2(mg, mg);
 #pragma unroll
           for (int j = 0; j < RH; ++j) {
             const int t = i - j;
             if (t >= 0 && t < T) {
-              cc[j] = fmaf(g[t], mg, cc[j]);
-              cp[j] = fmaf(gp[t], mg, cp[j]);
-              cp[j] = fmaf(g[t], mp, cp[j]);
-              bb[j] = fmaf(g[t], mb, bb[j]);
+              ccp[j] = __ffma2_rn(gg[t], mm, ccp[j]);
+              ccp[j].y = fmaf(gg[t].x, mp, ccp[j].y);
+              bb[j] = fmaf(gg[t].x, mb, bb[j]);
             }
           }
         }
@@ -232,9 +241,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
           const int ctr = (hy + S) * PS + hx0 + j + S;
           const float p = P[ctr], aq = Aqq[ctr];
           const float fq = den ? 1.f : Fq[ctr];
-          dacc[j] = fmaf(aq, cc[j], fmaf(fq, bb[j], dacc[j]));
+          dacc[j] = fmaf(aq, ccp[j].x, fmaf(fq, bb[j], dacc[j]));
           if (!den) dfa[qi][j] = fmaf(p, bb[j], dfa[qi][j]);
-          sig = fmaf(aq * p, cp[j], sig);
+          sig = fmaf(aq * p, ccp[j].y, sig);
         }
         __syncthreads();
       }
