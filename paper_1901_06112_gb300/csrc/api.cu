@@ -44,7 +44,7 @@ WsLayout ws_layout(const WsShape& s) {
   L.dphi = take(sizeof(float) * K * N);
   L.gpart = take(sizeof(float) * backward_gpart_floats(s.K));
   L.spart = take(sizeof(float) * backward_spart_floats(s.H, s.W, s.n));
-  L.gw = take(sizeof(double) * K * K);
+  L.gw = take(sizeof(double) * (2 * K * K + K));   // G_W, Z, row dots
   L.total = o;
   return L;
 }

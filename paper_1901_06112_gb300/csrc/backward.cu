@@ -178,18 +178,80 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
   }
 }
 
-// G_W[m][k] = sum over blocks (FP64, fixed order); one CTA per row m.
-__global__ void k_gw_reduce(const float* __restrict__ part, int nblk, int K,
-                            double* __restrict__ gw) {
-  const int m = blockIdx.x, k = threadIdx.x;
-  if (k >= K) return;
+// Z = (W_hat W_hat^T) X W_hat with X_ij = A_ij ||mu_i - mu_j||^2, one CTA per row
+// i.  With dL/dA = -1/2 W_hat W_hat^T G_W W_hat^T, the sigma_r term through A is
+//   sum_ij dL/dA_ij A_ij ||mu_i - mu_j||^2 / sigma_r^3 = -1/2 <G_W, Z> / sigma_r^3,
+// so Z (which does not depend on the incoming gradient) replaces three K^3
+// products after the reduction of G_W by one dot product per row.
+__global__ void __launch_bounds__(kMaxK)
+k_tail_z(int K, int rho, const float* __restrict__ lm, const float* __restrict__ what,
+         const double* __restrict__ A64, const DevState* __restrict__ state, double* __restrict__ Z) {
+  __shared__ double Mrow[kMaxK], MX[kMaxK];
+  const int i = blockIdx.x, t = threadIdx.x;
+  const int r = state->planes;
+  if (t < K) {
+    double s = 0.0;
+    for (int k = 0; k < r; ++k) s += (double)what[i * K + k] * (double)what[t * K + k];
+    Mrow[t] = s;
+  }
+  __syncthreads();
+  if (t < K) {
+    double s = 0.0;
+    for (int a = 0; a < K; ++a) {
+      double d2 = 0.0;
+      for (int d = 0; d < rho; ++d) {
+        const double u = (double)lm[a * rho + d] - (double)lm[t * rho + d];
+        d2 += u * u;
+      }
+      s += Mrow[a] * A64[a * K + t] * d2;
+    }
+    MX[t] = s;
+  }
+  __syncthreads();
+  if (t < K) {
+    double s = 0.0;
+    if (t < r)
+      for (int b = 0; b < K; ++b) s += MX[b] * (double)what[b * K + t];
+    Z[i * K + t] = s;
+  }
+}
+
+// G_W[m][k] = sum over blocks (FP64, fixed order: thread (g, k) sums blocks
+// g, g + G, ..., then the G group sums are added in order); one CTA per row m.
+// Also rowdot[m] = sum_k G_W[m][k] Z[m][k].
+__global__ void __launch_bounds__(256)
+k_gw_reduce(const float* __restrict__ part, int nblk, int K, const double* __restrict__ Z,
+            double* __restrict__ gw, double* __restrict__ rowdot) {
+  __shared__ double red[256];
+  __shared__ double prod[kMaxK];
+  const int m = blockIdx.x, tid = threadIdx.x;
+  const int G = 256 / K, g = tid / K, k = tid - g * K;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += (double)part[((int64_t)b * K + m) * K + k];
-  gw[m * K + k] = s;
+  if (g < G) {
+    const float* src = part + (int64_t)m * K + k;
+    const int64_t step = (int64_t)K * K;
+#pragma unroll 4
+    for (int b = g; b < nblk; b += G) s += (double)src[b * step];
+  }
+  red[tid] = s;
+  __syncthreads();
+  if (tid < K) {
+    double t = 0.0;
+    for (int q = 0; q < G; ++q) t += red[q * K + tid];
+    gw[m * K + tid] = t;
+    prod[tid] = t * Z[m * K + tid];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int q = 0; q < K; ++q) t += prod[q];
+    rowdot[m] = t;
+  }
 }
 
 // FP64 sum of `cnt` partials, fixed order (strided per thread, then a tree).
-__device__ double block_sum_fixed(const float* __restrict__ v, int64_t cnt, double* red) {
+template <typename T>
+__device__ double block_sum_fixed(const T* __restrict__ v, int64_t cnt, double* red) {
   const int tid = threadIdx.x;
   double s = 0.0;
   for (int64_t i = tid; i < cnt; i += blockDim.x) s += (double)v[i];
@@ -206,57 +268,15 @@ __device__ double block_sum_fixed(const float* __restrict__ v, int64_t cnt, doub
 
 // dsigma_r (through E and through A) and dsigma_s.
 __global__ void __launch_bounds__(256)
-k_bwd_tail(int K, int rho, const float* __restrict__ lm, float sigma_r, const float* __restrict__ what,
-           const double* __restrict__ gw, const double* __restrict__ A64,
+k_bwd_tail(int K, float sigma_r, const double* __restrict__ rowdot,
            const float* __restrict__ sr_part, int n_sr, const float* __restrict__ ss_part,
            int64_t n_ss, DevState* state, float* __restrict__ grad_sigma) {
   __shared__ double red[256];
-  extern __shared__ double dyn[];
-  double* T = dyn;                           // W_hat^T G_W   (K x K, rows/cols >= r zero)
-  double* U = dyn + K * K;                   // W_hat T
-  const int tid = threadIdx.x;
-  const int r = state->planes;
-  for (int e = tid; e < K * K; e += blockDim.x) {
-    const int a = e / K, b = e - a * K;
-    double s = 0.0;
-    if (a < r && b < r)
-      for (int m = 0; m < K; ++m) s += (double)what[m * K + a] * gw[m * K + b];
-    T[e] = s;
-  }
-  __syncthreads();
-  for (int e = tid; e < K * K; e += blockDim.x) {
-    const int i = e / K, b = e - i * K;
-    double s = 0.0;
-    if (b < r)
-      for (int a = 0; a < r; ++a) s += (double)what[i * K + a] * T[a * K + b];
-    U[e] = s;
-  }
-  __syncthreads();
   const double s3 = (double)sigma_r * sigma_r * sigma_r;
-  double acc = 0.0;
-  for (int e = tid; e < K * K; e += blockDim.x) {
-    const int i = e / K, j = e - i * K;
-    double dA = 0.0;
-    for (int b = 0; b < r; ++b) dA += U[i * K + b] * (double)what[j * K + b];
-    dA *= -0.5;
-    double d2 = 0.0;
-    for (int d = 0; d < rho; ++d) {
-      const double t = (double)lm[i * rho + d] - (double)lm[j * rho + d];
-      d2 += t * t;
-    }
-    acc += dA * A64[i * K + j] * d2;
-  }
-  red[tid] = acc;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (tid < o) red[tid] += red[tid + o];
-    __syncthreads();
-  }
-  const double through_A = red[0] / s3;
-  __syncthreads();
+  const double through_A = -0.5 * block_sum_fixed(rowdot, K, red) / s3;
   const double through_E = block_sum_fixed(sr_part, n_sr, red) / s3;
   const double dss = block_sum_fixed(ss_part, n_ss, red);
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     const float dsr = (float)(through_A + through_E);
     grad_sigma[0] = dsr;
     grad_sigma[1] = (float)dss;
@@ -358,20 +378,21 @@ cudaError_t launch_bwd_features(const float* f, const float* guide, int H, int W
   const float inv2s2r = (float)(1.0 / (2.0 * (double)sigma_r * sigma_r));
   float* gw_part = gpart;
   float* sr_part = gpart + (size_t)kFbBlocks * K * K;
+  double* Z = gw + (size_t)K * K;
+  double* rowdot = Z + (size_t)K * K;
+  k_tail_z<<<K, kMaxK, 0, st>>>(K, rho, landmarks, what, eig_A64(eig_scratch), state, Z);
+  count_launches(1);
   cudaError_t e;
   if (K <= 8) e = fb_rb<8>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);
   else if (K <= 16) e = fb_rb<16>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);
   else if (K <= 32) e = fb_rb<32>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);
   else e = fb_rb<64>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);
   if (e != cudaSuccess) return e;
-  k_gw_reduce<<<K, kMaxK, 0, st>>>(gw_part, kFbBlocks, K, gw);
+  k_gw_reduce<<<K, 256, 0, st>>>(gw_part, kFbBlocks, K, Z, gw, rowdot);
   count_launches(1);
   const int64_t n_ss = bwd_ctas(Sc, H, W, n);
-  const size_t smem = sizeof(double) * 2 * K * K;
-  e = cudaFuncSetAttribute(k_bwd_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_bwd_tail<<<1, 256, smem, st>>>(K, rho, landmarks, sigma_r, what, gw, eig_A64(eig_scratch),
-                                   sr_part, kFbBlocks, spart, n_ss, state, grad_sigma);
+  k_bwd_tail<<<1, 256, 0, st>>>(K, sigma_r, rowdot, sr_part, kFbBlocks, spart, n_ss, state,
+                                grad_sigma);
   count_launches(1);
   return cudaGetLastError();
 }

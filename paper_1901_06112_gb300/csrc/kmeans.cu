@@ -243,27 +243,33 @@ k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __
 }
 
 // One CTA per cluster j: FP64 sums of the block partials in a fixed order, then
-// the centroid moves to the mean of its members (kept if it has none).
+// the centroid moves to the mean of its members (kept if it has none).  The
+// rho + 1 sums run side by side: thread (g, d) sums partials b = g, g + G, ...
+// of coordinate d (d = rho is the count), then thread d adds the G group sums
+// in order.
 __global__ void __launch_bounds__(256)
 k_update(const float* __restrict__ part, int nblk, int rho, int K, float* __restrict__ cent) {
   __shared__ double red[256];
-  __shared__ double cnt;
+  __shared__ double sum[kMaxRho + 1];
   const int j = blockIdx.x, tid = threadIdx.x, stride = rho + 1;
-  for (int d = rho; d >= 0; --d) {       // count (d == rho) first
-    double s = 0.0;
-    for (int b = tid; b < nblk; b += 256) s += (double)part[((int64_t)b * K + j) * stride + d];
-    red[tid] = s;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (tid < o) red[tid] += red[tid + o];
-      __syncthreads();
-    }
-    if (tid == 0) {
-      if (d == rho) cnt = red[0];
-      else if (cnt > 0.0) cent[j * rho + d] = (float)(red[0] / cnt);
-    }
-    __syncthreads();
+  const int G = 256 / stride;
+  const int g = tid / stride, d = tid - g * stride;
+  double s = 0.0;
+  if (g < G) {
+    const float* src = part + (int64_t)j * stride + d;
+    const int64_t step = (int64_t)K * stride;
+#pragma unroll 4
+    for (int b = g; b < nblk; b += G) s += (double)src[b * step];
   }
+  red[tid] = s;
+  __syncthreads();
+  if (tid < stride) {
+    double t = 0.0;
+    for (int q = 0; q < G; ++q) t += red[q * stride + tid];
+    sum[tid] = t;
+  }
+  __syncthreads();
+  if (tid < rho && sum[rho] > 0.0) cent[j * rho + tid] = (float)(sum[tid] / sum[rho]);
 }
 
 // Quantisation error e = sum of the block partials (FP64, fixed order).
