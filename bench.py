@@ -195,11 +195,13 @@ def conv_flops_per_pixel(K, n, S):
 def conv_bwd_flops_per_pixel(K, n, S):
     """Algorithmic FLOPs of the adjoint convolutions per pixel.
 
-    Per plane: omega * (phi f), omega * (a phi) (2 passes each) and the sigma_s
-    term (g' (x) g + g (x) g') * (phi f) sharing the vertical g pass (3 more
-    passes): 7 passes x (2S + 1) taps x 2 FLOP, plus 6 FLOP of products.
+    The forward keeps C = omega * (phi f), so per plane the backward convolves
+    u = a phi with omega and with omega' = g' (x) g + g (x) g': a vertical
+    (g, g') pass and three horizontal passes (g and g' on the vertical g result,
+    g on the vertical g' result) = 5 passes x (2S + 1) taps x 2 FLOP, plus 10
+    FLOP of products (u; a C + f B; phi B; phi f B').
     """
-    return K * (n + 1) * (7 * (2 * S + 1) * 2 + 6)
+    return K * (n + 1) * (5 * (2 * S + 1) * 2 + 10)
 
 
 STAGES = ["landmarks", "eig", "features", "conv_combine", "bwd_conv", "bwd_features"]
@@ -284,11 +286,12 @@ def main():
     H, W, n = wl.f.shape
     fwdbwd = args.mode == "fwdbwd"
 
-    def make(precision):
+    def make(precision, bwd=False):
         return nyf.Params(sigma_s=wl.sigma_s, sigma_r=wl.sigma_r, K=wl.K,
-                          kmeans_iters=wl.kmeans_iters, seed=wl.seed + rank, precision=precision)
+                          kmeans_iters=wl.kmeans_iters, seed=wl.seed + rank, precision=precision,
+                          save_for_backward=bwd)
 
-    P = make(args.precision)
+    P = make(args.precision, fwdbwd)
     f_dev = torch.from_numpy(wl.f).to(dev)
     out = torch.empty_like(f_dev)
     ws = nyf.make_workspace(H, W, n, n, P, dev)
@@ -353,16 +356,18 @@ def main():
     extras = {}
     if not args.no_extras and rank == 0:
         lib.nyf_set_timing(0)
-        if fwdbwd:
-            fwd_ms, _ = timed_steps(make_step(P, False), max(3, args.steps // 2), flush, stream, lib)
+        if fwdbwd:                                # forward only: no planes kept
+            fwd_ms, _ = timed_steps(make_step(make(args.precision), False), max(3, args.steps // 2),
+                                    flush, stream, lib)
             extras["fwd"] = {"value": mp / (fwd_ms / 1e3), "ms_per_step": fwd_ms,
                              "unit": "megapixels/s", "precision": args.precision}
         other = "bf16" if args.precision == "fp32" else "fp32"
-        Po = make(other)
+        Po = make(other, fwdbwd)
         for _ in range(2):
             make_step(Po, fwdbwd)()
         o_ms, _ = timed_steps(make_step(Po, fwdbwd), max(3, args.steps // 2), flush, stream, lib)
-        f_ms, _ = timed_steps(make_step(Po, False), max(3, args.steps // 2), flush, stream, lib)
+        f_ms, _ = timed_steps(make_step(make(other), False), max(3, args.steps // 2), flush, stream,
+                              lib)
         extras[other] = {"fwdbwd_value" if fwdbwd else "value": mp / (o_ms / 1e3),
                          "fwd_value": mp / (f_ms / 1e3), "unit": "megapixels/s"}
         try:

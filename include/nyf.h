@@ -84,6 +84,11 @@ typedef struct {
   int patch_radius;   /* NLM: guide = (2r+1)^2 x n patch, reflect-101 border */
   float sample_frac;  /* fraction of pixels k-means clusters, (0, 1] */
   int conv_tile;      /* nyf_tile: convolution kernel variant */
+  int save_for_backward; /* nonzero: nyf_filter_blf also keeps, in the workspace, the
+                            K (n+1) convolved planes C_kq = omega * (phi_k f_q) that
+                            nyf_filter_blf_backward reads (the workspace grows by
+                            K (n+1) H W floats plus the backward scratch; see
+                            nyf_workspace_size).  Zero: forward-only workspace. */
 } nyf_params;
 
 /* Device-side results of the last call on a workspace (nyf_get_stats). */
@@ -165,7 +170,8 @@ nyf_status nyf_features_static(const float* guide, int64_t N, int rho, const flo
  *              of the guide (params->kmeans_iters, params->seed)
  *   out        H x W x n output g_hat = zeta / eta (device); pixels where
  *              eta_hat <= 0 are not clamped (Eq. (15) can vanish)
- * The workspace keeps the landmarks, factors, features and eta for
+ * The workspace keeps the landmarks, factors, features and eta, and with
+ * params->save_for_backward the convolved planes C_kq, for
  * nyf_filter_blf_backward. */
 nyf_status nyf_filter_blf(const float* f, const float* guide, int H, int W, int n, int rho,
                           const nyf_params* params, const float* landmarks, float* out,
@@ -183,7 +189,8 @@ nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params*
 
 /* Adjoint of nyf_filter_blf (the paper has no gradients; derived from
  * Eqs. (9)-(15)).  Must follow the nyf_filter_blf call that produced `out`
- * on the same workspace, with the same f, guide and params.  Landmarks are
+ * on the same workspace, with the same f, guide and params, and
+ * params->save_for_backward nonzero (else NYF_ERR_INVALID_ARG).  Landmarks are
  * held fixed; the window radius S is held at its forward value; the kept
  * modes are held fixed.  Given grad_out = dL/d g_hat (H x W x n):
  *   grad_f      H x W x n output dL/df; if guide was NULL this is the total

@@ -25,7 +25,8 @@ class NyfParams(C.Structure):
     _fields_ = [("sigma_s", C.c_float), ("sigma_r", C.c_float), ("K", C.c_int),
                 ("kmeans_iters", C.c_int), ("seed", C.c_uint64), ("eig_rel_tol", C.c_double),
                 ("precision", C.c_int), ("spatial", C.c_int), ("S", C.c_int),
-                ("patch_radius", C.c_int), ("sample_frac", C.c_float), ("conv_tile", C.c_int)]
+                ("patch_radius", C.c_int), ("sample_frac", C.c_float), ("conv_tile", C.c_int),
+                ("save_for_backward", C.c_int)]
 
 
 class NyfStats(C.Structure):

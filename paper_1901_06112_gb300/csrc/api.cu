@@ -41,10 +41,15 @@ WsLayout ws_layout(const WsShape& s) {
   L.phi = take((s.bf16 ? 2 : 4) * K * N);
   L.eta = take(sizeof(float) * N);
   L.zeta = take(sizeof(float) * N * (size_t)s.n);
-  L.dphi = take(sizeof(float) * K * N);
-  L.gpart = take(sizeof(float) * backward_gpart_floats(s.K));
-  L.spart = take(sizeof(float) * backward_spart_floats(s.H, s.W, s.n));
-  L.gw = take(sizeof(double) * (2 * K * K + K));   // G_W, Z, row dots
+  // backward only: dL/dphi, reduction partials, G_W / Z / row dots, the adjoint
+  // planes a_q and the forward's convolved planes C_kq
+  const size_t nq1 = (size_t)s.n + 1;
+  L.dphi = take(s.bwd ? sizeof(float) * K * N : 0);
+  L.gpart = take(s.bwd ? sizeof(float) * backward_gpart_floats(s.K) : 0);
+  L.spart = take(s.bwd ? sizeof(float) * backward_spart_floats(s.H, s.W, s.n) : 0);
+  L.gw = take(s.bwd ? sizeof(double) * (2 * K * K + K) : 0);
+  L.adj = take(s.bwd ? sizeof(float) * nq1 * N : 0);
+  L.cbuf = take(s.bwd ? sizeof(float) * K * nq1 * N : 0);
   L.total = o;
   return L;
 }
@@ -163,6 +168,7 @@ WsShape shape_for(int H, int W, int n, int rho, const nyf_params* p) {
   s.Ns = subsample_rows(s.N, p->sample_frac);
   s.bf16 = false;   // the filters keep phi in float32 (see nyf_params.precision)
   s.gather = p->patch_radius > 0;
+  s.bwd = p->save_for_backward != 0 && p->patch_radius == 0;
   return s;
 }
 
@@ -243,7 +249,9 @@ nyf_status blf_impl(const float* f, const float* guide, int H, int W, int n, int
     Stage t(st, 3, timed);
     NYF_TRY(launch_conv_combine(f, H, W, n, phi, false, tile, p->spatial, p->sigma_s, window_radius(p),
                                 state, out, reinterpret_cast<float*>(w + L.eta),
-                                reinterpret_cast<float*>(w + L.zeta), st));
+                                reinterpret_cast<float*>(w + L.zeta),
+                                p->save_for_backward ? reinterpret_cast<float*>(w + L.cbuf) : nullptr,
+                                st));
   }
   return NYF_OK;
 }
@@ -252,7 +260,7 @@ nyf_status blf_backward_impl(const float* f, const float* guide, int H, int W, i
                              const nyf_params* p, const float* out, const float* grad_out,
                              float* grad_f, float* grad_guide, float* grad_sigma, void* ws,
                              size_t ws_bytes, void* stream, bool timed) {
-  if (!p || p->patch_radius != 0) return NYF_ERR_INVALID_ARG;
+  if (!p || p->patch_radius != 0 || !p->save_for_backward) return NYF_ERR_INVALID_ARG;
   const bool tied = guide == nullptr || guide == f;
   if (tied) {
     if (rho != n) return NYF_ERR_INVALID_ARG;
@@ -276,8 +284,9 @@ nyf_status blf_backward_impl(const float* f, const float* guide, int H, int W, i
   {
     Stage t(st, 4, timed);
     NYF_TRY(launch_bwd_conv(f, H, W, n, p->K, p->spatial, p->sigma_s, S, w + L.phi, false,
-                            reinterpret_cast<const float*>(w + L.eta), out, grad_out, grad_f, dphi,
-                            spart, state, st));
+                            reinterpret_cast<const float*>(w + L.eta), out, grad_out,
+                            reinterpret_cast<const float*>(w + L.cbuf),
+                            reinterpret_cast<float*>(w + L.adj), grad_f, dphi, spart, state, st));
   }
   {
     Stage t(st, 5, timed);
@@ -461,7 +470,7 @@ nyf_status nyf_kmeans(const float* X, int64_t N, int rho, int K, int iters, uint
       K < 1 || K > NYF_MAX_K || K > N || iters < 0)
     return NYF_ERR_INVALID_ARG;
   if (kmeans_smem_bytes(K, rho) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
-  WsShape s{(int)N, 1, N, 1, rho, K, N, false, false};
+  WsShape s{(int)N, 1, N, 1, rho, K, N, false, false, false};
   const WsLayout L = ws_layout(s);
   if (!ws_ok(ws, ws_bytes, L.km_qpart + sizeof(float) * kKmeansBlocks)) return NYF_ERR_WORKSPACE;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -484,7 +493,7 @@ nyf_status nyf_features(const float* guide, int64_t N, int rho, const float* lan
       !(eig_rel_tol >= 0.0) || (precision != NYF_FP32 && precision != NYF_BF16))
     return NYF_ERR_INVALID_ARG;
   if (sizeof(float) * ((size_t)K * rho + (size_t)K * K) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
-  WsShape s{(int)N, 1, N, 1, rho, K, N, precision == NYF_BF16, false};
+  WsShape s{(int)N, 1, N, 1, rho, K, N, precision == NYF_BF16, false, false};
   const WsLayout L = ws_layout(s);
   if (!ws_ok(ws, ws_bytes, L.eig + eig_scratch_bytes())) return NYF_ERR_WORKSPACE;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -546,7 +555,7 @@ nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params*
     Stage t(st, 3);
     NYF_TRY(launch_conv_combine(f, H, W, n, phi, false, tile, p->spatial, p->sigma_s, window_radius(p),
                                 state, out, reinterpret_cast<float*>(w + L.eta),
-                                reinterpret_cast<float*>(w + L.zeta), st));
+                                reinterpret_cast<float*>(w + L.zeta), nullptr, st));
   }
   return NYF_OK;
 }

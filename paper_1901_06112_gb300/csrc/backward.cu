@@ -285,6 +285,22 @@ k_bwd_tail(int K, float sigma_r, const double* __restrict__ rowdot,
   }
 }
 
+// dL/d zeta_q as planes: a_c = G_c / eta (c < n), a_n = -sum_c G_c g_hat_c / eta.
+__global__ void k_adjoint(const float* __restrict__ gout, const float* __restrict__ out,
+                          const float* __restrict__ eta, int64_t N, int n, float* __restrict__ adj) {
+  for (int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pix < N;
+       pix += (int64_t)gridDim.x * blockDim.x) {
+    const float ie = 1.f / eta[pix];
+    float s = 0.f;
+    for (int c = 0; c < n; ++c) {
+      const float g = gout[pix * n + c];
+      adj[(int64_t)c * N + pix] = g * ie;
+      s = fmaf(g, out[pix * n + c], s);
+    }
+    adj[(int64_t)n * N + pix] = -s * ie;
+  }
+}
+
 template <int KB, int RB>
 cudaError_t fb_launch(const float* guide, int64_t N, int rho, const float* lm, int K, float inv2s2r,
                       const float* what, const DevState* state, const float* dphi, float* dguide,
@@ -326,11 +342,15 @@ const double* eig_A64(const void* scratch);
 
 cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spatial, float sigma_s,
                             int S, const void* phi, bool bf16, const float* eta, const float* out,
-                            const float* grad_out, float* grad_f, float* dphi, float* spart,
-                            const DevState* state, cudaStream_t st) {
+                            const float* grad_out, const float* cbuf, float* adj, float* grad_f,
+                            float* dphi, float* spart, const DevState* state, cudaStream_t st) {
   const int Sc = conv_compiled_radius(S);
   if (Sc < 0) return cudaErrorInvalidValue;
   const int64_t N = (int64_t)H * W;
+  int64_t g = (N + 255) / 256;
+  if (g > 152 * 16) g = 152 * 16;
+  k_adjoint<<<(int)g, 256, 0, st>>>(grad_out, out, eta, N, n, adj);
+  count_launches(1);
   const int chunks = bwd_chunks(Sc, n);
   cudaError_t e;
   if (chunks > 1) {
@@ -346,9 +366,8 @@ cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spat
   a.phi = phi;
   a.bf16 = bf16 ? 1 : 0;
   a.state = state;
-  a.eta = eta;
-  a.out = out;
-  a.gout = grad_out;
+  a.adj = adj;
+  a.cbuf = cbuf;
   a.box = spatial == NYF_BOX ? 1 : 0;
   a.inv2s2 = a.box ? 0.f : (float)(1.0 / (2.0 * (double)sigma_s * sigma_s));
   a.inv_s3 = a.box ? 0.f : (float)(1.0 / ((double)sigma_s * sigma_s * sigma_s));

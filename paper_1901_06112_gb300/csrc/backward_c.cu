@@ -17,7 +17,7 @@ cudaError_t bwd_dispatch_c(int Sc, const BwdArgs& a, cudaStream_t st) {
 }
 
 int bwd_chunks(int Sc, int n) {
-  const int nq = Sc <= 24 ? 2 : 1;
+  const int nq = Sc <= 16 ? 4 : 2;
   return (n + 1 + nq - 1) / nq;
 }
 

@@ -4,21 +4,24 @@
 //   C_kq = omega * (phi_k f_q),  zeta_q = sum_k phi_k C_kq,  g_hat_c = zeta_c / eta,
 //   eta = zeta_n.
 // With G = dL/d g_hat:  a_c = G_c / eta (c < n),  a_n = -sum_c G_c g_hat_c / eta, so
-// dL/d zeta_q = a_q.  Writing B_kq = omega * (a_q phi_k) (omega is symmetric, so
-// the adjoint of the convolution is the convolution itself):
+// dL/d zeta_q = a_q.  Writing u_kq = a_q phi_k and B_kq = omega * u_kq (omega is
+// symmetric, so the adjoint of the zero-padded convolution is the convolution
+// itself):
 //   dL/d phi_k(x) = sum_q [ a_q(x) C_kq(x) + f_q(x) B_kq(x) ]            (f_n := 1)
 //   dL/d f_c(x)  += sum_k phi_k(x) B_kc(x)                     (direct image term)
-//   dL/d sigma_s  = sum_x sum_q a_q(x) sum_k phi_k(x) (omega' * (phi_k f_q))(x),
+//   dL/d sigma_s  = sum_kq sum_x u_kq(x) (omega' * (phi_k f_q))(x)
+//                 = sum_kq sum_x (phi_k f_q)(x) (omega' * u_kq)(x),
 // where omega' = d omega / d sigma_s = g' (x) g + g (x) g' with
-// g'(t) = g(t) t^2 / sigma_s^3 (window radius held fixed).
+// g'(t) = g(t) t^2 / sigma_s^3 (window radius held fixed).  The forward pass
+// saves C_kq, so the backward convolves only u_kq, with g and g' together:
+// vertical pass (g, g') on u, horizontal pass B = g * Mb, B' = g' * Mb + g * Mb'.
 //
-// One CTA per (output tile, pair of quantities).  Per mode k the CTA stages
-// phi_k (double-buffered, cp.async) and runs, per quantity, one vertical pass
-// producing three planes (g on phi f, g' on phi f, g on a phi) and one
-// horizontal pass producing C, the sigma_s term and B at its pixels.  dL/dphi_k
-// leaves the CTA as one plane per mode (summed with atomics when the
-// quantities of a pixel are split over several CTAs), dL/df and the sigma_s
-// partial at the end.
+// One CTA per output tile holds all quantities of its pixels (up to four), so
+// dL/dphi_k leaves the CTA as one plane per mode without atomics.  Per mode k
+// the CTA stages phi_k once, runs the vertical pass of every quantity in one
+// balanced task list, then streams phi_{k+1} in while the horizontal pass and
+// the epilogue run.  Lanes of a warp own consecutive rows in the horizontal
+// pass (conflict-free shared-memory reads), warps own column segments.
 #pragma once
 
 #include "conv_impl.cuh"
@@ -32,34 +35,35 @@ struct BwdArgs {
   const void* phi;
   int bf16;
   const DevState* state;
-  const float* eta;       // N, saved by the forward pass
-  const float* out;       // g_hat, N x n
-  const float* gout;      // dL/d g_hat, N x n
+  const float* adj;       // (n + 1) planes of N: a_q
+  const float* cbuf;      // K (n + 1) planes of N: C_kq (plane k (n + 1) + q), saved by the forward
   float inv2s2;           // 1 / (2 sigma_s^2)
   float inv_s3;           // 1 / sigma_s^3
   int S_true;
   int box;
   float* dphi;            // r planes of N
-  int atomic_dphi;
+  int atomic_dphi;        // quantities split over several CTAs: accumulate dphi atomically
   float* df;              // N x n, direct image term
   float* sig_part;        // one sigma_s partial per CTA
 };
 
 template <int S>
 struct BwdCfg {
-  static constexpr int TH = 32;
+  static constexpr int TH = 32;                                 // = lanes: one row per lane
   static constexpr int TW = S <= 16 ? 64 : (S <= 24 ? 48 : 32);
-  static constexpr int RV = S <= 24 ? 16 : 8;
-  static constexpr int RH = S <= 16 ? 8 : (S <= 24 ? 6 : 4);
-  static constexpr int NQ = S <= 24 ? 2 : 1;
+  static constexpr int RV = 16;
+  static constexpr int NQ = S <= 16 ? 4 : 2;                    // quantities per CTA
+  static constexpr int RH = TW / (kConvThreads / 32);           // columns per thread
   static constexpr int HH = TH + 2 * S;
   static constexpr int HW = TW + 2 * S;
   static constexpr int PS = HW | 1;
   static constexpr int PLANE = HH * PS;
-  static constexpr int VT = (TH / RV) * HW;          // vertical tasks
+  static constexpr int VB = TH / RV;                            // vertical row blocks
+  static constexpr int VT = NQ * VB * HW;                       // vertical tasks
   static constexpr size_t smem =
-      sizeof(float) * ((size_t)(2 * NQ + 2) * PLANE + (size_t)3 * TH * PS);
-  static_assert(TH * (TW / RH) == kConvThreads, "one horizontal task per thread");
+      sizeof(float) * ((size_t)(NQ + 1) * PLANE + (size_t)2 * NQ * TH * PS);
+  static_assert(TH == 32 && RH * (kConvThreads / 32) == TW, "lane = row, warp = segment");
+  static_assert(((NQ + 1) * PLANE) % 2 == 0, "float2 alignment of the vertical planes");
   static_assert(smem <= 227 * 1024, "shared memory budget");
 };
 
@@ -95,52 +99,30 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
   constexpr int TH = C::TH, TW = C::TW, RV = C::RV, RH = C::RH, NQ = C::NQ;
   constexpr int HH = C::HH, HW = C::HW, PS = C::PS, PLANE = C::PLANE;
   extern __shared__ float sm[];
-  float* F = sm;                    // NQ image planes
-  float* Aq = F + NQ * PLANE;       // NQ adjoint planes a_q
-  float* PB = Aq + NQ * PLANE;      // two phi planes
-  float* Mg = PB + 2 * PLANE;       // vertical passes: g on phi f
-  float* Mp = Mg + TH * PS;         //                  g' on phi f
-  float* Mb = Mp + TH * PS;         //                  g on a phi
-  const int tid = threadIdx.x;
+  float* Aq = sm;                                              // NQ adjoint planes
+  float* P = Aq + NQ * PLANE;                                  // phi_k
+  float2* M = reinterpret_cast<float2*>(P + PLANE);            // NQ x TH x PS: (g, g') on u
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
   const int q0 = blockIdx.z * NQ;
   const int n = a.n;
+  const int nq = min(NQ, n + 1 - q0);                          // quantities of this CTA
   const int r = a.state->planes;
 
+  // adjoint planes a_q on the tile + halo (zero outside the image), then phi_0
   for (int e = tid; e < NQ * HH * HW; e += kConvThreads) {
     const int qi = e / (HH * HW);
     const int rem = e - qi * (HH * HW);
     const int yy = rem / HW, xx = rem - yy * HW;
-    const int c = q0 + qi;
     const int gy = ty0 - S + yy, gx = tx0 - S + xx;
-    const bool in = c < n && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
-    cp_async4(F + qi * PLANE + yy * PS + xx, in ? a.f + ((int64_t)gy * a.W + gx) * n + c : a.f, in);
+    const bool in = qi < nq && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+    cp_async4(Aq + qi * PLANE + yy * PS + xx,
+              in ? a.adj + (int64_t)(q0 + qi) * a.N + (int64_t)gy * a.W + gx : a.adj, in);
   }
-  if (r > 0) bwd_stage_phi<S>(a, PB, 0, ty0, tx0);
+  if (r > 0) bwd_stage_phi<S>(a, P, 0, ty0, tx0);
   cp_async_commit();
-  // a_q on the tile + halo (zero outside the image)
-  for (int e = tid; e < NQ * HH * HW; e += kConvThreads) {
-    const int qi = e / (HH * HW);
-    const int rem = e - qi * (HH * HW);
-    const int yy = rem / HW, xx = rem - yy * HW;
-    const int q = q0 + qi;
-    const int gy = ty0 - S + yy, gx = tx0 - S + xx;
-    float v = 0.f;
-    if (q <= n && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W) {
-      const int64_t pix = (int64_t)gy * a.W + gx;
-      const float ie = 1.f / a.eta[pix];
-      if (q < n) {
-        v = a.gout[pix * n + q] * ie;
-      } else {
-        float s = 0.f;
-        for (int c = 0; c < n; ++c) s = fmaf(a.gout[pix * n + c], a.out[pix * n + c], s);
-        v = -s * ie;
-      }
-    }
-    Aq[qi * PLANE + yy * PS + xx] = v;
-  }
 
-  // (g, g') tap pairs: one packed FMA updates the g and g' accumulators of an input
+  // (g, g') tap pairs: one packed FMA updates the g and g' sums of an input
   float2 gg[T];
 #pragma unroll
   for (int t = 0; t < T; ++t) {
@@ -151,6 +133,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
     gg[t] = make_float2(gv, (on && !a.box) ? gv * zz * a.inv_s3 : 0.f);
   }
 
+  const int hy = lane, hx0 = warp * RH;
+  const int y = ty0 + hy;
+  const bool yin = y < a.H;
+  // image channels at this thread's pixels (f_n := 1 for the denominator)
+  float fc[NQ][RH];
+#pragma unroll
+  for (int qi = 0; qi < NQ; ++qi)
+#pragma unroll
+    for (int j = 0; j < RH; ++j) {
+      const int q = q0 + qi, x = tx0 + hx0 + j;
+      fc[qi][j] = q < n ? ((yin && x < a.W) ? a.f[((int64_t)y * a.W + x) * n + q] : 0.f) : 1.f;
+    }
   float dfa[NQ][RH];
 #pragma unroll
   for (int qi = 0; qi < NQ; ++qi)
@@ -158,97 +152,97 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
     for (int j = 0; j < RH; ++j) dfa[qi][j] = 0.f;
   float sig = 0.f;
 
-  const int hy = tid / (TW / RH), hx0 = (tid % (TW / RH)) * RH;
-  const int y = ty0 + hy;
-
   for (int k = 0; k < r; ++k) {
-    if (k + 1 < r) {
-      bwd_stage_phi<S>(a, PB + ((k + 1) & 1) * PLANE, k + 1, ty0, tx0);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+    cp_async_wait<0>();
+    __syncthreads();                 // phi_k (and the adjoint planes) landed; M is free
+    float pc[RH];                    // phi_k at this thread's pixels
+#pragma unroll
+    for (int j = 0; j < RH; ++j) pc[j] = P[(hy + S) * PS + hx0 + j + S];
+
+    // vertical pass of every quantity: (g, g') on u = a_q phi_k
+    for (int task = tid; task < C::VT; task += kConvThreads) {
+      const int qi = task / (C::VB * HW);
+      const int rem = task - qi * (C::VB * HW);
+      const int vb = rem / HW, vx = rem - vb * HW;
+      const int vy0 = vb * RV;
+      if (qi < nq) {
+        const float* A = Aq + qi * PLANE;
+        float2 vm[RV];
+#pragma unroll
+        for (int j = 0; j < RV; ++j) vm[j] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < RV + 2 * S; ++i) {
+          const int off = (vy0 + i) * PS + vx;
+          const float u = P[off] * A[off];
+          const float2 uu = make_float2(u, u);
+#pragma unroll
+          for (int j = 0; j < RV; ++j) {
+            const int t = i - j;
+            if (t >= 0 && t < T) vm[j] = __ffma2_rn(gg[t], uu, vm[j]);
+          }
+        }
+        float2* Mq = M + qi * (TH * PS);
+#pragma unroll
+        for (int j = 0; j < RV; ++j) Mq[(vy0 + j) * PS + vx] = vm[j];
+      }
     }
-    __syncthreads();
-    const float* P = PB + (k & 1) * PLANE;
+    __syncthreads();                 // M complete; nobody reads P beyond this point
+    if (k + 1 < r) {                 // phi_{k+1} streams in under the horizontal pass
+      bwd_stage_phi<S>(a, P, k + 1, ty0, tx0);
+      cp_async_commit();
+    }
+
     float dacc[RH];
 #pragma unroll
     for (int j = 0; j < RH; ++j) dacc[j] = 0.f;
 #pragma unroll
     for (int qi = 0; qi < NQ; ++qi) {
-      const int q = q0 + qi;
-      if (q <= n) {                              // uniform over the block
-        const bool den = (q == n);
-        const float* Fq = F + qi * PLANE;
-        const float* Aqq = Aq + qi * PLANE;
-        for (int task = tid; task < C::VT; task += kConvThreads) {
-          const int vx = task % HW, vy0 = (task / HW) * RV;
-          float2 vap[RV];            // (g, g') on phi f
-          float vb[RV];              // g on a phi
+      if (qi < nq) {                 // uniform over the block
+        const int q = q0 + qi;
+        // C_kq at this thread's pixels, saved by the forward pass
+        const float* Cp = a.cbuf + ((int64_t)k * (n + 1) + q) * a.N + (int64_t)y * a.W + tx0 + hx0;
+        float cq[RH];
+        if (RH % 4 == 0 && yin && tx0 + hx0 + RH <= a.W &&
+            (reinterpret_cast<uintptr_t>(Cp) & 15) == 0) {
 #pragma unroll
-          for (int j = 0; j < RV; ++j) {
-            vap[j] = make_float2(0.f, 0.f);
-            vb[j] = 0.f;
+          for (int m = 0; m < RH / 4; ++m) {
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(Cp) + m);
+            cq[4 * m] = v.x;
+            cq[4 * m + 1] = v.y;
+            cq[4 * m + 2] = v.z;
+            cq[4 * m + 3] = v.w;
           }
+        } else {
 #pragma unroll
-          for (int i = 0; i < RV + 2 * S; ++i) {
-            const int off = (vy0 + i) * PS + vx;
-            const float p = P[off];
-            const float h = den ? p : p * Fq[off];
-            const float u = p * Aqq[off];
-            const float2 hh = make_float2(h, h);
-#pragma unroll
-            for (int j = 0; j < RV; ++j) {
-              const int t = i - j;
-              if (t >= 0 && t < T) {
-                vap[j] = __ffma2_rn(gg[t], hh, vap[j]);
-                vb[j] = fmaf(gg[t].x, u, vb[j]);
-              }
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < RV; ++j) {
-            Mg[(vy0 + j) * PS + vx] = vap[j].x;
-            Mp[(vy0 + j) * PS + vx] = vap[j].y;
-            Mb[(vy0 + j) * PS + vx] = vb[j];
-          }
+          for (int j = 0; j < RH; ++j) cq[j] = (yin && tx0 + hx0 + j < a.W) ? __ldcs(Cp + j) : 0.f;
         }
-        __syncthreads();
-        float2 ccp[RH];              // (g on Mg, g' on Mg + g on Mp)
-        float bb[RH];
+        const float2* Mq = M + qi * (TH * PS) + hy * PS + hx0;
+        float2 bp[RH];               // (B, B') at this thread's pixels
 #pragma unroll
-        for (int j = 0; j < RH; ++j) {
-          ccp[j] = make_float2(0.f, 0.f);
-          bb[j] = 0.f;
-        }
+        for (int j = 0; j < RH; ++j) bp[j] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < RH + 2 * S; ++i) {
-          const int off = hy * PS + hx0 + i;
-          const float mg = Mg[off], mp = Mp[off], mb = Mb[off];
-          const float2 mm = make_float2(mg, mg);
+          const float2 m = Mq[i];
+          const float2 mm = make_float2(m.x, m.x);
 #pragma unroll
           for (int j = 0; j < RH; ++j) {
             const int t = i - j;
             if (t >= 0 && t < T) {
-              ccp[j] = __ffma2_rn(gg[t], mm, ccp[j]);
-              ccp[j].y = fmaf(gg[t].x, mp, ccp[j].y);
-              bb[j] = fmaf(gg[t].x, mb, bb[j]);
+              bp[j] = __ffma2_rn(gg[t], mm, bp[j]);        // (g Mb, g' Mb)
+              bp[j].y = fmaf(gg[t].x, m.y, bp[j].y);        //  + g Mb'
             }
           }
         }
+        const float* Ac = Aq + qi * PLANE + (hy + S) * PS + hx0 + S;
 #pragma unroll
         for (int j = 0; j < RH; ++j) {
-          const int ctr = (hy + S) * PS + hx0 + j + S;
-          const float p = P[ctr], aq = Aqq[ctr];
-          const float fq = den ? 1.f : Fq[ctr];
-          dacc[j] = fmaf(aq, ccp[j].x, fmaf(fq, bb[j], dacc[j]));
-          if (!den) dfa[qi][j] = fmaf(p, bb[j], dfa[qi][j]);
-          sig = fmaf(aq * p, ccp[j].y, sig);
+          dacc[j] = fmaf(Ac[j], cq[j], fmaf(fc[qi][j], bp[j].x, dacc[j]));
+          dfa[qi][j] = fmaf(pc[j], bp[j].x, dfa[qi][j]);
+          sig = fmaf(pc[j] * fc[qi][j], bp[j].y, sig);
         }
-        __syncthreads();
       }
     }
-    if (y < a.H) {
+    if (yin) {
       float* dst = a.dphi + (int64_t)k * a.N + (int64_t)y * a.W;
 #pragma unroll
       for (int j = 0; j < RH; ++j) {
@@ -262,7 +256,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
   }
   cp_async_wait<0>();
 
-  if (y < a.H) {
+  if (yin) {
 #pragma unroll
     for (int j = 0; j < RH; ++j) {
       const int x = tx0 + hx0 + j;
@@ -278,7 +272,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
   __shared__ float red[kConvThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
-  if ((tid & 31) == 0) red[tid >> 5] = sig;
+  if (lane == 0) red[warp] = sig;
   __syncthreads();
   if (tid == 0) {
     float s = 0.f;
@@ -289,21 +283,20 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
 }
 
 template <int S>
+dim3 bwd_grid(int H, int W, int n) {
+  using C = BwdCfg<S>;
+  return dim3((W + C::TW - 1) / C::TW, (H + C::TH - 1) / C::TH, (n + 1 + C::NQ - 1) / C::NQ);
+}
+
+template <int S>
 cudaError_t bwd_launch(const BwdArgs& a, cudaStream_t st) {
   using C = BwdCfg<S>;
   cudaError_t e = cudaFuncSetAttribute(k_conv_bwd<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)C::smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((a.W + C::TW - 1) / C::TW, (a.H + C::TH - 1) / C::TH, (a.n + 1 + C::NQ - 1) / C::NQ);
-  k_conv_bwd<S><<<grid, kConvThreads, C::smem, st>>>(a);
+  k_conv_bwd<S><<<bwd_grid<S>(a.H, a.W, a.n), kConvThreads, C::smem, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
-}
-
-template <int S>
-dim3 bwd_grid(int H, int W, int n) {
-  using C = BwdCfg<S>;
-  return dim3((W + C::TW - 1) / C::TW, (H + C::TH - 1) / C::TH, (n + 1 + C::NQ - 1) / C::NQ);
 }
 
 cudaError_t bwd_dispatch_a(int Sc, const BwdArgs& a, cudaStream_t st);   // 1..8

@@ -42,7 +42,8 @@ bool conv_split(int S, int n) {
 
 cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void* phi, bool bf16,
                                 int tile, int spatial, float sigma_s, int S, DevState* state,
-                                float* out, float* eta_out, float* zeta_ws, cudaStream_t st) {
+                                float* out, float* eta_out, float* zeta_ws, float* cout,
+                                cudaStream_t st) {
   const int Sc = conv_compiled_radius(S);
   if (Sc < 0) return cudaErrorInvalidValue;
   ConvArgs a;
@@ -68,6 +69,7 @@ cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void*
   a.out = split ? nullptr : out;
   a.zeta = split ? zeta_ws : nullptr;
   a.eta = eta_out;
+  a.cout = cout;
   cudaError_t e;
   if (mma) e = conv_mma_dispatch(a, st);
   else if (Sc <= 8) e = conv_dispatch_a(Sc, a, st);

@@ -6,8 +6,9 @@
 // as a separable FIR (vertical pass into shared memory, then horizontal pass
 // into registers) and accumulates zeta_q += phi_k C_kq in registers; eta is
 // the q = n accumulator.  Only g_hat = zeta / eta (or zeta and eta when the
-// quantities are split over several CTAs) leaves the chip: the K (n+1)
-// convolved planes never touch HBM.
+// quantities are split over several CTAs) leaves the chip, plus, when the
+// caller will run the backward pass, the K (n+1) convolved planes C_kq
+// (written once here instead of being recomputed there).
 //
 // Zero padding outside the image is the window clipping of Eq. (1).  The taps
 // g(z) = exp(-z^2 / (2 sigma_s^2)) (or 1 for the box) are held in registers;
@@ -35,6 +36,7 @@ struct ConvArgs {
   float* zeta;              // N x n, when they are split
   float* eta;               // N
   int narrow;               // FP32 kernel: 32 x 64 tiles instead of 32 x 96 (S <= 16)
+  float* cout;              // K (n + 1) planes C_kq (plane k (n + 1) + q) for the backward pass, or NULL
 };
 
 constexpr int kConvThreads = 256;
@@ -103,6 +105,32 @@ __device__ __forceinline__ void stage_phi(const ConvArgs& a, float* P, int k, in
 }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Store RH consecutive values of two planes (v[j].x to ca[j], v[j].y to cb[j]
+// unless cb is NULL) for the `valid` leading columns: 16-byte streaming stores
+// when the row segment is whole and aligned, else one float at a time.
+template <int RH>
+__device__ __forceinline__ void store_pair_row(float* ca, float* cb, const float2* v, int valid) {
+  const bool vec = (RH % 4 == 0) && valid >= RH &&
+                   ((reinterpret_cast<uintptr_t>(ca) | reinterpret_cast<uintptr_t>(cb)) & 15) == 0;
+  if (vec) {
+#pragma unroll
+    for (int m = 0; m < RH / 4; ++m) {
+      __stcs(reinterpret_cast<float4*>(ca) + m,
+             make_float4(v[4 * m].x, v[4 * m + 1].x, v[4 * m + 2].x, v[4 * m + 3].x));
+      if (cb)
+        __stcs(reinterpret_cast<float4*>(cb) + m,
+               make_float4(v[4 * m].y, v[4 * m + 1].y, v[4 * m + 2].y, v[4 * m + 3].y));
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < RH; ++j)
+      if (j < valid) {
+        ca[j] = v[j].x;
+        if (cb) cb[j] = v[j].y;
+      }
+  }
+}
 
 template <int S, bool WIDE>
 __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
@@ -212,6 +240,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
         for (int j = 0; j < RH; ++j) {
           const float p = P[(hy + S) * PS + hx0 + j + S];
           acc[pi][j] = __ffma2_rn(f2(p, p), hb[j], acc[pi][j]);
+        }
+        if (a.cout && ty0 + hy < a.H) {          // keep C_kq for the backward pass
+          float* ca = a.cout + ((int64_t)k * (n + 1) + qa) * a.N + (int64_t)(ty0 + hy) * a.W + tx0 + hx0;
+          store_pair_row<RH>(ca, b_none ? nullptr : ca + a.N, hb, a.W - (tx0 + hx0));
         }
         __syncthreads();
       }

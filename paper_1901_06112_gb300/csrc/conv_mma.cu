@@ -243,6 +243,23 @@ __global__ void __launch_bounds__(kMmaThreads, 1) k_conv_combine_mma(ConvArgs a)
         acc[nb][1] = fmaf(P[y0 * C::FS + x0 + 1], o[1], acc[nb][1]);
         acc[nb][2] = fmaf(P[(y0 + 8) * C::FS + x0], o[2], acc[nb][2]);
         acc[nb][3] = fmaf(P[(y0 + 8) * C::FS + x0 + 1], o[3], acc[nb][3]);
+        if (a.cout) {                              // keep C_kq for the backward pass
+          float* cq = a.cout + ((int64_t)k * (n + 1) + q) * a.N;
+          const int gy = ty0 + 16 * rb + g, gx = tx0 + 8 * nb + 2 * t;
+          const bool pair = gx + 1 < a.W && (a.W & 1) == 0;   // 8-byte aligned column pair
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (gy + 8 * h < a.H) {
+              float* row = cq + (int64_t)(gy + 8 * h) * a.W + gx;
+              if (pair) {
+                __stcs(reinterpret_cast<float2*>(row), make_float2(o[2 * h], o[2 * h + 1]));
+              } else {
+                if (gx < a.W) row[0] = o[2 * h];
+                if (gx + 1 < a.W) row[1] = o[2 * h + 1];
+              }
+            }
+          }
+        }
       }
     }
     __syncthreads();

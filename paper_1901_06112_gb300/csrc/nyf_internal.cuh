@@ -32,7 +32,7 @@ struct DevState {
 // Byte offsets of every region of a workspace (all 256-byte aligned).
 struct WsLayout {
   size_t state, landmarks, what, eig, init_idx, km_part, km_qpart, sample_idx, sample_x, phi,
-      eta, zeta, dphi, gpart, spart, gw, total;
+      eta, zeta, dphi, gpart, spart, gw, adj, cbuf, total;
 };
 
 // Problem geometry used to size a workspace.
@@ -45,6 +45,7 @@ struct WsShape {
   int64_t Ns;       // rows k-means clusters
   bool bf16;        // features stored as bfloat16
   bool gather;      // k-means rows are gathered (subsample or NLM patches)
+  bool bwd;         // regions of the backward pass (saved convolutions, adjoints, partials)
 };
 
 WsLayout ws_layout(const WsShape& s);
@@ -91,13 +92,14 @@ cudaError_t launch_features_nlm(const float* f, int H, int W, int n, int r, cons
 size_t features_nlm_smem_bytes(int K, int n, int r);
 cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void* phi, bool bf16,
                                 int tile, int spatial, float sigma_s, int S, DevState* state,
-                                float* out, float* eta_out, float* zeta_ws, cudaStream_t st);
+                                float* out, float* eta_out, float* zeta_ws, float* cout,
+                                cudaStream_t st);
 int conv_compiled_radius(int S);
 bool conv_split(int S, int n);
 cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spatial, float sigma_s,
                             int S, const void* phi, bool bf16, const float* eta, const float* out,
-                            const float* grad_out, float* grad_f, float* dphi, float* spart,
-                            const DevState* state, cudaStream_t st);
+                            const float* grad_out, const float* cbuf, float* adj, float* grad_f,
+                            float* dphi, float* spart, const DevState* state, cudaStream_t st);
 cudaError_t launch_bwd_features(const float* f, const float* guide, int H, int W, int n, int rho,
                                 const float* landmarks, int K, float sigma_r, int S,
                                 const float* what, const float* dphi, float* grad_f,

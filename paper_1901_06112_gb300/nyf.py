@@ -32,6 +32,7 @@ class Params:
     patch_radius: int = 0          # NLM patch radius
     sample_frac: float = 1.0
     conv_tile: str = "auto"        # "auto" | "wide" | "narrow" | "tensor"
+    save_for_backward: bool = False  # forward keeps the convolved planes for blf_backward
 
     def c(self) -> L.NyfParams:
         return L.NyfParams(float(self.sigma_s), float(self.sigma_r), int(self.K),
@@ -41,7 +42,12 @@ class Params:
                            L.BOX if self.spatial == "box" else L.GAUSSIAN, int(self.S),
                            int(self.patch_radius), float(self.sample_frac),
                            {"auto": L.TILE_AUTO, "wide": L.TILE_WIDE, "narrow": L.TILE_NARROW,
-                            "tensor": L.TILE_TENSOR}[self.conv_tile])
+                            "tensor": L.TILE_TENSOR}[self.conv_tile],
+                           1 if self.save_for_backward else 0)
+
+    def for_backward(self) -> "Params":
+        """A copy whose forward keeps what the backward pass reads."""
+        return Params(**{**self.__dict__, "save_for_backward": True})
 
     @property
     def radius(self) -> int:
@@ -188,7 +194,8 @@ def blf_backward_available() -> bool:
 
 def blf_backward(f, params: Params, out, grad_out, ws: Workspace, bufs: BackwardBuffers = None,
                  guide=None) -> BackwardBuffers:
-    """Adjoint of blf(): must follow the forward call that produced `out` on `ws`.
+    """Adjoint of blf(): must follow the forward call that produced `out` on `ws`,
+    made with params.save_for_backward set (Params.for_backward()).
 
     Landmarks, the window radius and the kept modes are held at their forward
     values.  Returns the buffers (grad_f is the total derivative when the guide
@@ -209,6 +216,7 @@ def blf_backward(f, params: Params, out, grad_out, ws: Workspace, bufs: Backward
 
 def blf_vjp(f, params: Params, grad_out, guide=None, landmarks=None) -> dict:
     """Forward + backward: gradients of sum(grad_out * g_hat)."""
+    params = params.for_backward()
     H, W, n = f.shape
     rho = n if guide is None else guide.shape[2]
     ws = make_workspace(H, W, n, rho, params, f.device)
@@ -227,7 +235,7 @@ class NyfBLF(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, f, guide, sigma_r, sigma_s, params: Params, landmarks=None):
-        P = Params(**{**params.__dict__})
+        P = params.for_backward()
         P.sigma_r = float(sigma_r)
         P.sigma_s = float(sigma_s)
         f = f.contiguous()
@@ -275,10 +283,11 @@ class Batched:
              "tensor": L.TILE_TENSOR}
 
     def __init__(self, shapes, sigmas_s, sigmas_r, params: Params, n=3, device="cuda",
-                 tiles=None):
+                 tiles=None, backward=True):
         self.lib = L.load()
         self.B = len(shapes)
         self.n = n
+        params = params.for_backward() if backward else params
         self.params = params
         self.items = (L.NyfBatchItem * self.B)()
         off = 0

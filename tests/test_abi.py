@@ -37,6 +37,10 @@ def test_workspace_size_host_logic(lib):
     p.K = 0
     assert lib.nyf_workspace_size(256, 256, 3, 3, C.byref(p)) == 0
     p.K = 8
+    p.save_for_backward = 1   # the forward keeps K (n + 1) convolved planes for the backward
+    sb = lib.nyf_workspace_size(256, 256, 3, 3, C.byref(p))
+    assert sb >= s1 + 4 * 8 * 4 * 256 * 256
+    p.save_for_backward = 0
     p.patch_radius = 2        # NLM: rho is derived from n and r
     assert lib.nyf_workspace_size(64, 64, 3, 1, C.byref(p)) > 0
 
@@ -61,6 +65,9 @@ def test_argument_errors_return_before_any_launch(lib):
                               1 << 30, None) == 3
     # guide dimension must equal n when the guide is the image
     assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 2, C.byref(p), None, bad, bad, 1 << 30, None) == 1
+    # the backward needs a forward that kept its convolved planes
+    assert lib.nyf_filter_blf_backward(bad, None, 8, 8, 3, 3, C.byref(p), bad, bad, bad, None, bad,
+                                       bad, 1 << 30, None) == 1
     # k-means: more clusters than rows
     assert lib.nyf_kmeans(bad, 4, 3, 8, 1, 0, None, bad, None, None, bad, 1 << 20, None) == 1
 

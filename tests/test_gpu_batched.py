@@ -48,7 +48,7 @@ def test_batched_equals_per_image_calls(nyf, precision):
     torch.cuda.synchronize()
     for b, (H, W) in enumerate(shapes):
         Pb = nyf.Params(sigma_s=ss[b], sigma_r=sr[b], K=6, kmeans_iters=4, seed=3,
-                        precision=precision)
+                        precision=precision, save_for_backward=True)
         fb = torch.from_numpy(imgs[b]).cuda()
         ws = nyf.make_workspace(H, W, 3, 3, Pb)
         ob = nyf.blf(fb, Pb, ws=ws)
