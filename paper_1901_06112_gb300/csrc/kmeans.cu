@@ -104,12 +104,27 @@ __global__ void k_draw_init(const float* __restrict__ X, int64_t N, int rho, int
   }
 }
 
-// Assignment pass.  RB > 0: the rows are held in registers (rho <= RB) and
-// each thread handles PPT rows, so one centroid load from shared memory serves
-// PPT distance evaluations; RB == 0: rows are re-read from global memory
-// (large rho, used for small row counts).
+template <int R, int PPT, int RX>
+__device__ __forceinline__ void unpack_rows(const float* buf, float (&x)[PPT][RX]) {
+#pragma unroll
+  for (int q = 0; q < PPT; ++q)
+#pragma unroll
+    for (int d = 0; d < RX; ++d) x[q][d] = d < R ? buf[q * R + d] : 0.f;
+}
+
+// Assignment pass.  RB > 0: each thread holds PPT consecutive rows in
+// registers (rho <= RB), so one centroid load from shared memory serves PPT
+// distance evaluations, evaluated two rows at a time with packed FP32x2
+// arithmetic (x - c as x + (-c), then the same fused multiply-adds as one row
+// at a time, so the distances are bitwise those of the scalar form).  Rows of a
+// thread that share a label are summed in the thread first (image rows are
+// spatially coherent), then every label present in the warp is reduced across
+// the lanes once.  RB == 0: rows are re-read from global memory (large rho,
+// used for small row counts).
 // part[b][j][0..rho) = sum of the members of cluster j seen by block b,
 // part[b][j][rho] = their count; qpart[b] = sum of their squared distances.
+// Every sum runs in an order fixed by the data layout, so results are bitwise
+// reproducible.
 template <int RB, int THREADS, int PPT>
 __global__ void __launch_bounds__(THREADS)
 k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __restrict__ cent,
@@ -132,23 +147,50 @@ k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __
   __syncthreads();
 
   float qsum = 0.f;
-  for (int64_t base = (int64_t)blockIdx.x * THREADS * PPT; base < N;
-       base += (int64_t)gridDim.x * THREADS * PPT) {
-    float x[PPT][RX];
-    bool valid[PPT];
-    int best[PPT];
-    float bd[PPT];
+  if (RB > 0) {
+    for (int64_t base = (int64_t)blockIdx.x * THREADS * PPT; base < N;
+         base += (int64_t)gridDim.x * THREADS * PPT) {
+      const int64_t i0 = base + (int64_t)tid * PPT;       // this thread's first row
+      float x[PPT][RX];
+      bool valid[PPT];
+      int best[PPT];
+      float bd[PPT];
+      const float* xi = X + (i0 < N ? i0 : 0) * rho;
+      const bool vec = RB == 4 && i0 + PPT <= N && (PPT * rho) % 4 == 0 &&
+                       (reinterpret_cast<uintptr_t>(xi) & 15) == 0;
+      if (vec) {                                          // PPT rows = rho float4 loads
+        float buf[PPT * RX];
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      const int64_t i = base + (int64_t)q * THREADS + tid;
-      valid[q] = i < N;
-      const float* xi = X + (valid[q] ? i : 0) * rho;
+        for (int v = 0; v < RX; ++v) {
+          if (v < rho) {
+            const float4 w = __ldg(reinterpret_cast<const float4*>(xi) + v);
+            buf[4 * v] = w.x;
+            buf[4 * v + 1] = w.y;
+            buf[4 * v + 2] = w.z;
+            buf[4 * v + 3] = w.w;
+          }
+        }
+        switch (rho) {                                    // row q, coordinate d = buf[q rho + d]
+          case 1: unpack_rows<1, PPT, RX>(buf, x); break;
+          case 2: unpack_rows<2, PPT, RX>(buf, x); break;
+          case 3: unpack_rows<3, PPT, RX>(buf, x); break;
+          default: unpack_rows<4, PPT, RX>(buf, x); break;
+        }
+      } else {
 #pragma unroll
-      for (int d = 0; d < RX; ++d) x[q][d] = (RB > 0 && d < rho) ? __ldg(xi + d) : 0.f;
-      best[q] = 0;
-      bd[q] = __int_as_float(0x7f800000);
-    }
-    if (RB > 0) {
+        for (int q = 0; q < PPT; ++q) {
+          const bool ok = i0 + q < N;
+          const float* r = X + (ok ? i0 + q : 0) * rho;
+#pragma unroll
+          for (int d = 0; d < RX; ++d) x[q][d] = (ok && d < rho) ? __ldg(r + d) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) {
+        valid[q] = i0 + q < N;
+        best[q] = 0;
+        bd[q] = __int_as_float(0x7f800000);
+      }
 #pragma unroll 4
       for (int j = 0; j < K; ++j) {
         const float* m = mu + j * ms;
@@ -163,20 +205,99 @@ k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __
 #pragma unroll
           for (int d = 0; d < RX; ++d) c[d] = d < rho ? m[d] : 0.f;
         }
+        if (PPT >= 2) {
+          float2 nc[RX];
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) {
+          for (int d = 0; d < RX; ++d) nc[d] = make_float2(-c[d], -c[d]);
+#pragma unroll
+          for (int pr = 0; pr < PPT / 2; ++pr) {
+            float2 t = __fadd2_rn(make_float2(x[2 * pr][0], x[2 * pr + 1][0]), nc[0]);
+            float2 dist = __fmul2_rn(t, t);
+#pragma unroll
+            for (int d = 1; d < RX; ++d) {
+              t = __fadd2_rn(make_float2(x[2 * pr][d], x[2 * pr + 1][d]), nc[d]);
+              dist = __ffma2_rn(t, t, dist);
+            }
+            // strict: ties keep the lowest index
+            if (dist.x < bd[2 * pr]) { bd[2 * pr] = dist.x; best[2 * pr] = j; }
+            if (dist.y < bd[2 * pr + 1]) { bd[2 * pr + 1] = dist.y; best[2 * pr + 1] = j; }
+          }
+        } else {
           float dist = 0.f;
 #pragma unroll
           for (int d = 0; d < RX; ++d) {
-            const float t = x[q][d] - c[d];
+            const float t = x[0][d] - c[d];
             dist = fmaf(t, t, dist);
           }
-          if (dist < bd[q]) { bd[q] = dist; best[q] = j; }   // strict: ties keep the lowest index
+          if (dist < bd[0]) { bd[0] = dist; best[0] = j; }
         }
       }
-    } else {
+#pragma unroll
+      for (int q = 0; q < PPT; ++q)
+        if (valid[q]) {
+          qsum += bd[q];
+          if (labels) labels[i0 + q] = best[q];
+        }
+      if (accumulate) {
+        // merge this thread's rows by label (fixed order), then one warp
+        // reduction per label present in the warp
+        int cnt[PPT];
+        bool live[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+          cnt[q] = 1;
+          live[q] = valid[q];
+        }
+#pragma unroll
+        for (int q = 1; q < PPT; ++q)
+#pragma unroll
+          for (int p = 0; p < q; ++p)
+            if (live[p] && live[q] && best[p] == best[q]) {
+#pragma unroll
+              for (int d = 0; d < RX; ++d) x[p][d] += x[q][d];
+              cnt[p] += cnt[q];
+              live[q] = false;
+            }
+        for (int guard = 0; guard < 32 * PPT; ++guard) {
+          int my = K;
+#pragma unroll
+          for (int q = PPT - 1; q >= 0; --q)
+            if (live[q]) my = best[q];
+          const unsigned any = __ballot_sync(kFull, my < K);
+          if (!any) break;
+          const int L = __shfl_sync(kFull, my, __ffs(any) - 1);
+          float v[RX];
+          int c = 0;
+#pragma unroll
+          for (int d = 0; d < RX; ++d) v[d] = 0.f;
+#pragma unroll
+          for (int q = 0; q < PPT; ++q)
+            if (live[q] && best[q] == L) {
+#pragma unroll
+              for (int d = 0; d < RX; ++d) v[d] = x[q][d];
+              c = cnt[q];
+              live[q] = false;
+            }
+          float* a = acc + (warp * K + L) * stride;
+#pragma unroll
+          for (int d = 0; d < RX; ++d) {
+            if (d < rho) {
+              const float s = warp_sum(v[d]);
+              if (lane == 0) a[d] += s;
+            }
+          }
+          const unsigned total = __reduce_add_sync(kFull, (unsigned)c);
+          if (lane == 0) a[rho] += (float)total;
+        }
+      }
+    }
+  } else {
+    for (int64_t base = (int64_t)blockIdx.x * THREADS; base < N; base += (int64_t)gridDim.x * THREADS) {
       const int64_t i = base + tid;
-      const float* xi = X + (valid[0] ? i : 0) * rho;
+      const bool valid = i < N;
+      const float* xi = X + (valid ? i : 0) * rho;
+      int best = 0;
+      float bd = __int_as_float(0x7f800000);
       for (int j = 0; j < K; ++j) {
         const float* m = mu + j * ms;
         float dist = 0.f;
@@ -184,38 +305,23 @@ k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __
           const float t = __ldg(xi + d) - m[d];
           dist = fmaf(t, t, dist);
         }
-        if (dist < bd[0]) { bd[0] = dist; best[0] = j; }
+        if (dist < bd) { bd = dist; best = j; }
       }
-    }
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      const int64_t i = base + (int64_t)q * THREADS + tid;
-      const float* xi = X + (valid[q] ? i : 0) * rho;
-      if (valid[q]) {
-        qsum += bd[q];
-        if (labels) labels[i] = best[q];
+      if (valid) {
+        qsum += bd;
+        if (labels) labels[i] = best;
       }
       if (accumulate) {
-        unsigned todo = __ballot_sync(kFull, valid[q]);
+        unsigned todo = __ballot_sync(kFull, valid);
         while (todo) {
           const int leader = __ffs(todo) - 1;
-          const int L = __shfl_sync(kFull, best[q], leader);
-          const bool mine = valid[q] && best[q] == L;
+          const int L = __shfl_sync(kFull, best, leader);
+          const bool mine = valid && best == L;
           const unsigned grp = __ballot_sync(kFull, mine);
           float* a = acc + (warp * K + L) * stride;
-          if (RB > 0) {
-#pragma unroll
-            for (int d = 0; d < RX; ++d) {
-              if (d < rho) {
-                const float v = warp_sum(mine ? x[q][d] : 0.f);
-                if (lane == 0) a[d] += v;
-              }
-            }
-          } else {
-            for (int d = 0; d < rho; ++d) {
-              const float v = warp_sum(mine ? __ldg(xi + d) : 0.f);
-              if (lane == 0) a[d] += v;
-            }
+          for (int d = 0; d < rho; ++d) {
+            const float v = warp_sum(mine ? __ldg(xi + d) : 0.f);
+            if (lane == 0) a[d] += v;
           }
           if (lane == 0) a[rho] += (float)__popc(grp);
           todo &= ~grp;
