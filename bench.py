@@ -4,9 +4,10 @@
 Workload (default): the 1920 x 1080 x 3 colour bilateral filter -- 400
 Voronoi cells with sinusoidal shading and noise 15, sigma_s 5 (31 x 31
 window), sigma_r 40, K 32 k-means landmarks (10 Lloyd iterations).  One step
-is one pass of the whole path on one image: subsample/k-means, FP64
-eigendecomposition, features, convolutions + combine (and the backward pass
-when --mode fwdbwd).  Inputs are resident in HBM; L2 is flushed between steps.
+is one pass of the whole path on one image: k-means, FP64-accurate
+eigendecomposition, features, convolutions + combine, then (default
+--mode fwdbwd) the backward pass w.r.t. the image, sigma_r and sigma_s.
+Inputs are resident in HBM; L2 is flushed between steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
                        [--mode fwd|fwdbwd] [--impl nyf|reference]
@@ -54,6 +55,11 @@ def parse():
 # ----------------------------------------------------------------------------- CPU oracle leg
 
 CPU_SAMPLE = (192, 192)     # crop of the workload the oracle filters (and differentiates) per step
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the FP32 kernels on the
+# 1920 x 1080, K = 32 workload, from the ncu capture summarised in
+# profiles/ncu_conv_kernels_colour_blf_1920x1080.md; valid for the kernels as captured.
+NCU_TRAFFIC = {"conv_bwd": 1.420e9 + 0.253e9, "conv_combine": 0.323e9 + 1.035e9}
 
 
 def _oracle_step_code(h, w, backward):
@@ -342,11 +348,13 @@ def main():
     fwd_flops = conv_flops_per_pixel(planes, n, P.radius) * H * W
     bwd_flops = conv_bwd_flops_per_pixel(planes, n, P.radius) * H * W
 
+    captured = args.precision == "fp32" and (H, W, wl.K) == (1080, 1920, 32)
+
     def roof(name, flops, ms_k):
         a = flops / (ms_k / 1e3) / 1e12
         return {"kernel": name, "bound": "alu" if args.precision == "fp32" or name != "conv_combine"
                 else "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
-                "traffic": None, "launch_ms": ms_k,
+                "traffic": NCU_TRAFFIC.get(name) if captured else None, "launch_ms": ms_k,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FP32 ALU)"}
 
     roof_fwd = roof("conv_combine", fwd_flops, stage_mean[3])
