@@ -372,6 +372,21 @@ cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spat
   a.inv2s2 = a.box ? 0.f : (float)(1.0 / (2.0 * (double)sigma_s * sigma_s));
   a.inv_s3 = a.box ? 0.f : (float)(1.0 / ((double)sigma_s * sigma_s * sigma_s));
   a.S_true = S;
+  // taps of the window and their sigma_s derivative, g'(z) = g(z) z^2 / sigma_s^3,
+  // zero beyond the true radius (the compiled radius Sc may be larger)
+  for (int z = -kMaxTapRadius; z <= kMaxTapRadius; ++z) {
+    float2 t = make_float2(0.f, 0.f);
+    if (z >= -S && z <= S) {
+      if (a.box) {
+        t.x = 1.f;
+      } else {
+        const double s = (double)sigma_s, g = exp(-(double)z * z / (2.0 * s * s));
+        t.x = (float)g;
+        t.y = (float)(g * z * z / (s * s * s));
+      }
+    }
+    a.taps[kMaxTapRadius + z] = t;
+  }
   a.dphi = dphi;
   a.atomic_dphi = chunks > 1 ? 1 : 0;
   a.df = grad_f;

@@ -21,7 +21,8 @@
 // the CTA stages phi_k once, runs the vertical pass of every quantity in one
 // balanced task list, then streams phi_{k+1} in while the horizontal pass and
 // the epilogue run.  Lanes of a warp own consecutive rows in the horizontal
-// pass (conflict-free shared-memory reads), warps own column segments.
+// pass (conflict-free shared-memory reads), warps own column segments.  The
+// taps come from the launch parameters (constant bank) instead of registers.
 #pragma once
 
 #include "conv_impl.cuh"
@@ -45,7 +46,10 @@ struct BwdArgs {
   int atomic_dphi;        // quantities split over several CTAs: accumulate dphi atomically
   float* df;              // N x n, direct image term
   float* sig_part;        // one sigma_s partial per CTA
+  float2 taps[2 * kMaxTapRadius + 1];   // (g(z), g'(z)) for z = -S_compiled..S_compiled, zero beyond S
 };
+
+constexpr int kBwdThreads = 256;    // 8 warps; the taps live in the launch parameters (constant bank)
 
 template <int S>
 struct BwdCfg {
@@ -53,7 +57,7 @@ struct BwdCfg {
   static constexpr int TW = S <= 16 ? 64 : (S <= 24 ? 48 : 32);
   static constexpr int RV = 16;
   static constexpr int NQ = S <= 16 ? 4 : 2;                    // quantities per CTA
-  static constexpr int RH = TW / (kConvThreads / 32);           // columns per thread
+  static constexpr int RH = TW / (kBwdThreads / 32);            // columns per thread
   static constexpr int HH = TH + 2 * S;
   static constexpr int HW = TW + 2 * S;
   static constexpr int PS = HW | 1;
@@ -62,7 +66,7 @@ struct BwdCfg {
   static constexpr int VT = NQ * VB * HW;                       // vertical tasks
   static constexpr size_t smem =
       sizeof(float) * ((size_t)(NQ + 1) * PLANE + (size_t)2 * NQ * TH * PS);
-  static_assert(TH == 32 && RH * (kConvThreads / 32) == TW, "lane = row, warp = segment");
+  static_assert(TH == 32 && RH * (kBwdThreads / 32) == TW, "lane = row, warp = segment");
   static_assert(((NQ + 1) * PLANE) % 2 == 0, "float2 alignment of the vertical planes");
   static_assert(smem <= 227 * 1024, "shared memory budget");
 };
@@ -73,7 +77,7 @@ __device__ __forceinline__ void bwd_stage_phi(const BwdArgs& a, float* P, int k,
   const int64_t base = (int64_t)k * a.N;
   if (!a.bf16) {
     const float* src = reinterpret_cast<const float*>(a.phi) + base;
-    for (int e = threadIdx.x; e < C::HH * C::HW; e += kConvThreads) {
+    for (int e = threadIdx.x; e < C::HH * C::HW; e += kBwdThreads) {
       const int yy = e / C::HW, xx = e - yy * C::HW;
       const int gy = ty0 - S + yy, gx = tx0 - S + xx;
       const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
@@ -81,7 +85,7 @@ __device__ __forceinline__ void bwd_stage_phi(const BwdArgs& a, float* P, int k,
     }
   } else {
     const __nv_bfloat16* src = reinterpret_cast<const __nv_bfloat16*>(a.phi) + base;
-    for (int e = threadIdx.x; e < C::HH * C::HW; e += kConvThreads) {
+    for (int e = threadIdx.x; e < C::HH * C::HW; e += kBwdThreads) {
       const int yy = e / C::HW, xx = e - yy * C::HW;
       const int gy = ty0 - S + yy, gx = tx0 - S + xx;
       float v = 0.f;
@@ -93,7 +97,7 @@ __device__ __forceinline__ void bwd_stage_phi(const BwdArgs& a, float* P, int k,
 }
 
 template <int S>
-__global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_constant__ BwdArgs a) {
   using C = BwdCfg<S>;
   constexpr int T = 2 * S + 1;
   constexpr int TH = C::TH, TW = C::TW, RV = C::RV, RH = C::RH, NQ = C::NQ;
@@ -110,7 +114,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
   const int r = a.state->planes;
 
   // adjoint planes a_q on the tile + halo (zero outside the image), then phi_0
-  for (int e = tid; e < NQ * HH * HW; e += kConvThreads) {
+  for (int e = tid; e < NQ * HH * HW; e += kBwdThreads) {
     const int qi = e / (HH * HW);
     const int rem = e - qi * (HH * HW);
     const int yy = rem / HW, xx = rem - yy * HW;
@@ -122,16 +126,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
   if (r > 0) bwd_stage_phi<S>(a, P, 0, ty0, tx0);
   cp_async_commit();
 
-  // (g, g') tap pairs: one packed FMA updates the g and g' sums of an input
-  float2 gg[T];
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int z = t - S;
-    const float zz = (float)(z * z);
-    const bool on = !(z > a.S_true || -z > a.S_true);
-    const float gv = on ? (a.box ? 1.f : expf(-zz * a.inv2s2)) : 0.f;
-    gg[t] = make_float2(gv, (on && !a.box) ? gv * zz * a.inv_s3 : 0.f);
-  }
+  // (g, g') tap pairs from the launch parameters: one packed FMA updates the g
+  // and g' sums of an input
+  const float2* gg = a.taps + (kMaxTapRadius - S);
 
   const int hy = lane, hx0 = warp * RH;
   const int y = ty0 + hy;
@@ -160,7 +157,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
     for (int j = 0; j < RH; ++j) pc[j] = P[(hy + S) * PS + hx0 + j + S];
 
     // vertical pass of every quantity: (g, g') on u = a_q phi_k
-    for (int task = tid; task < C::VT; task += kConvThreads) {
+    for (int task = tid; task < C::VT; task += kBwdThreads) {
       const int qi = task / (C::VB * HW);
       const int rem = task - qi * (C::VB * HW);
       const int vb = rem / HW, vx = rem - vb * HW;
@@ -269,14 +266,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_bwd(BwdArgs a) {
     }
   }
   // sigma_s partial of this CTA (fixed-order reduction)
-  __shared__ float red[kConvThreads / 32];
+  __shared__ float red[kBwdThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
   if (lane == 0) red[warp] = sig;
   __syncthreads();
   if (tid == 0) {
     float s = 0.f;
-    for (int w = 0; w < kConvThreads / 32; ++w) s += red[w];
+    for (int w = 0; w < kBwdThreads / 32; ++w) s += red[w];
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     a.sig_part[cta] = s;
   }
@@ -294,7 +291,7 @@ cudaError_t bwd_launch(const BwdArgs& a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_conv_bwd<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)C::smem);
   if (e != cudaSuccess) return e;
-  k_conv_bwd<S><<<bwd_grid<S>(a.H, a.W, a.n), kConvThreads, C::smem, st>>>(a);
+  k_conv_bwd<S><<<bwd_grid<S>(a.H, a.W, a.n), kBwdThreads, C::smem, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -59,6 +59,12 @@ cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void*
   a.box = spatial == NYF_BOX ? 1 : 0;
   a.inv2s2 = a.box ? 0.f : (float)(1.0 / (2.0 * (double)sigma_s * (double)sigma_s));
   a.S_true = S;
+  for (int z = -kMaxTapRadius; z <= kMaxTapRadius; ++z) {
+    float g = 0.f;
+    if (z >= -S && z <= S)
+      g = a.box ? 1.f : (float)exp(-(double)z * z / (2.0 * (double)sigma_s * (double)sigma_s));
+    a.taps[kMaxTapRadius + z] = make_float2(g, g);
+  }
   double mass = 0.0;   // full-window mass of omega
   for (int z = -S; z <= S; ++z) mass += a.box ? 1.0 : exp(-(double)z * z * a.inv2s2);
   a.eta_thr = (float)(1e-6 * mass * mass);

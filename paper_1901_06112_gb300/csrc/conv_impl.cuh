@@ -11,9 +11,10 @@
 // (written once here instead of being recomputed there).
 //
 // Zero padding outside the image is the window clipping of Eq. (1).  The taps
-// g(z) = exp(-z^2 / (2 sigma_s^2)) (or 1 for the box) are held in registers;
-// the window radius S is a compile-time bound (taps with |z| above the true
-// radius are zero) so that the register-blocked FIR loops fully unroll.
+// g(z) = exp(-z^2 / (2 sigma_s^2)) (or 1 for the box) come from the launch
+// parameters (constant bank); the window radius S is a compile-time bound
+// (taps with |z| above the true radius are zero) so that the register-blocked
+// FIR loops fully unroll.
 #pragma once
 
 #include "nyf_internal.cuh"
@@ -37,9 +38,11 @@ struct ConvArgs {
   float* eta;               // N
   int narrow;               // FP32 kernel: 32 x 64 tiles instead of 32 x 96 (S <= 16)
   float* cout;              // K (n + 1) planes C_kq (plane k (n + 1) + q) for the backward pass, or NULL
+  float2 taps[2 * NYF_MAX_S + 1];   // (g(z), g(z)) for z = -32..32, zero beyond the true radius
 };
 
 constexpr int kConvThreads = 256;
+constexpr int kMaxTapRadius = NYF_MAX_S;   // tap arrays in launch parameters cover -32..32
 
 // Tile shapes by radius class.  TH x TW output pixels per CTA; the vertical
 // pass gives each thread RV rows of one halo column, the horizontal pass RH
@@ -133,7 +136,7 @@ __device__ __forceinline__ void store_pair_row(float* ca, float* cb, const float
 }
 
 template <int S, bool WIDE>
-__global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_constant__ ConvArgs a) {
   using C = ConvCfg<S, WIDE>;
   constexpr int T = 2 * S + 1;
   constexpr int TH = C::TH, TW = C::TW, RV = C::RV, RH = C::RH, NQ = C::NQ;
@@ -163,14 +166,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(ConvArgs a) {
   if (r > 0) stage_phi<S, WIDE>(a, PB, 0, ty0, tx0);
   cp_async_commit();
 
-  float2 g[T];
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int z = t - S;
-    const float zz = (float)(z * z);
-    const float v = (z > a.S_true || -z > a.S_true) ? 0.f : (a.box ? 1.f : expf(-zz * a.inv2s2));
-    g[t] = f2(v, v);
-  }
+  const float2* g = a.taps + (kMaxTapRadius - S);   // (g, g) pairs, from the constant bank
 
   float2 acc[NP][RH];
 #pragma unroll
