@@ -203,6 +203,17 @@ nyf_status nyf_filter_blf_backward(const float* f, const float* guide, int H, in
                                    const float* grad_out, float* grad_f, float* grad_guide,
                                    float* grad_sigma, void* ws, size_t ws_bytes, void* stream);
 
+/* Self-test of the fifth-generation tensor-core path the BF16 convolutions use
+ * (the paper has no counterpart): one CTA computes D = A B^T, M = 128,
+ * N in {16, 32, ..., 256}, K in {16, 32, ..., 128}, from operands the kernel
+ * generates, A[m][k] = (((3m + 5k) mod 17) - 8) / 8 and
+ * B[n][k] = (((7n + 3k) mod 13) - 6) / 4 (exact in bfloat16), with tcgen05.mma
+ * accumulating in tensor memory.
+ *   D       128 x N float32 output (device, row-major)
+ *   status  1 int output (device): 0, or 1 if the MMA completion wait timed out
+ * Returns NYF_ERR_INVALID_ARG for other sizes. */
+nyf_status nyf_selftest_umma(float* D, int N, int K, int* status, void* stream);
+
 /* ---- Batched filtering of images of uneven sizes (one workload, one call).
  * Image b of the batch is the H_b x W_b x n HWC block starting at element
  * items[b].offset of the packed buffers f / out / grad_out / grad_f (device);

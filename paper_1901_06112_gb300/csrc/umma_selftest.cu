@@ -1,0 +1,90 @@
+// Self-test of the tcgen05 building blocks (umma.cuh): one CTA computes
+// D = A B^T for M = 128, N in {16, ..., 256}, K in {16, ..., 128} from operands
+// generated in the kernel (small integers over powers of two, exact in
+// bfloat16), with the accumulator in tensor memory.  The caller compares D with
+// the same product computed on the host.  The paper has no counterpart; this
+// checks the tensor-core plumbing the BF16 convolutions build on.
+#include "nyf_internal.cuh"
+#include "umma.cuh"
+
+namespace nyf {
+namespace {
+
+constexpr uint32_t kWaitLimit = 1u << 22;   // mbarrier polls before giving up
+
+__host__ __device__ inline float st_a(int m, int k) { return (float)(((m * 3 + k * 5) % 17) - 8) * 0.125f; }
+__host__ __device__ inline float st_b(int n, int k) { return (float)(((n * 7 + k * 3) % 13) - 6) * 0.25f; }
+
+__global__ void __launch_bounds__(128, 1) k_umma_selftest(float* __restrict__ D, int N, int K,
+                                                         int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int M = 128;
+  unsigned char* A = sm;                       // M x K, K-major core matrices
+  unsigned char* B = sm + M * K * 2;           // N x K
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < M * K; e += blockDim.x) {
+    const int m = e / K, k = e - m * K;
+    *reinterpret_cast<__nv_bfloat16*>(A + umma::kmajor_offset(m, k, K)) = __float2bfloat16(st_a(m, k));
+  }
+  for (int e = tid; e < N * K; e += blockDim.x) {
+    const int n = e / K, k = e - n * K;
+    *reinterpret_cast<__nv_bfloat16*>(B + umma::kmajor_offset(n, k, K)) = __float2bfloat16(st_b(n, k));
+  }
+  umma::fence_async_smem();
+  uint32_t ncols = 32;
+  while ((int)ncols < N) ncols <<= 1;
+  if (warp == 0) umma::tmem_alloc(&tmem_slot, ncols);
+  if (tid == 0) {
+    umma::mbar_init(&mbar, 1);
+    umma::fence_mbar_init();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tbase = tmem_slot;
+  if (tid == 0) {
+    const uint32_t a0 = umma::smem_u32(A), b0 = umma::smem_u32(B);
+    const uint32_t sbo = (uint32_t)K * 16;
+    for (int ks = 0; ks < K / 16; ++ks)
+      umma::mma_bf16(tbase, umma::sdesc(a0 + ks * 256, 128, sbo), umma::sdesc(b0 + ks * 256, 128, sbo),
+                     umma::idesc_bf16(M, N), ks > 0 ? 1u : 0u);
+    umma::commit(&mbar);
+  }
+  const bool ok = umma::mbar_wait(&mbar, 0, kWaitLimit);
+  umma::fence_after_sync();
+  if (!ok && lane == 0) atomicExch(status, 1);
+  if (ok) {
+    for (int c0 = 0; c0 < N; c0 += 32) {
+      float v[32];
+      umma::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+      const int m = 32 * warp + lane;
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (c0 + i < N) D[m * N + c0 + i] = v[i];
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tbase, ncols);
+}
+
+}  // namespace
+}  // namespace nyf
+
+using namespace nyf;
+
+extern "C" nyf_status nyf_selftest_umma(float* D, int N, int K, int* status, void* stream) {
+  if (!D || !status || N < 16 || N > 256 || (N & 15) || K < 16 || K > 128 || (K & 15))
+    return NYF_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t smem = (size_t)(128 + N) * K * 2;
+  if (cudaFuncSetAttribute(k_umma_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return NYF_ERR_CUDA;
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return NYF_ERR_CUDA;
+  k_umma_selftest<<<1, 128, smem, st>>>(D, N, K, status);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? NYF_OK : NYF_ERR_CUDA;
+}
