@@ -209,10 +209,11 @@ nyf_status nyf_filter_blf_backward(const float* f, const float* guide, int H, in
  * generates, A[m][k] = (((3m + 5k) mod 17) - 8) / 8 and
  * B[n][k] = (((7n + 3k) mod 13) - 6) / 4 (exact in bfloat16), with tcgen05.mma
  * accumulating in tensor memory.
- *   D       128 x N float32 output (device, row-major)
- *   status  1 int output (device): 0, or 1 if the MMA completion wait timed out
+ *   D          128 x N float32 output (device, row-major)
+ *   a_in_tmem  0: A in shared memory; 1: A in tensor memory (bf16 pairs per column)
+ *   status     1 int output (device): 0, or 1 if the MMA completion wait timed out
  * Returns NYF_ERR_INVALID_ARG for other sizes. */
-nyf_status nyf_selftest_umma(float* D, int N, int K, int* status, void* stream);
+nyf_status nyf_selftest_umma(float* D, int N, int K, int a_in_tmem, int* status, void* stream);
 
 /* ---- Batched filtering of images of uneven sizes (one workload, one call).
  * Image b of the batch is the H_b x W_b x n HWC block starting at element

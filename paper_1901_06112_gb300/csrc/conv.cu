@@ -21,8 +21,8 @@ __global__ void k_divide(const float* __restrict__ zeta, const float* __restrict
 
 }  // namespace
 
-cudaError_t conv_mma_dispatch(const ConvArgs& a, cudaStream_t st);
-bool conv_mma_split(int n);
+cudaError_t conv_tc_dispatch(const ConvArgs& a, cudaStream_t st);
+bool conv_tc_supported(int S, int n);
 
 // Smallest compiled radius >= S.
 int conv_compiled_radius(int S) {
@@ -68,16 +68,16 @@ cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void*
   double mass = 0.0;   // full-window mass of omega
   for (int z = -S; z <= S; ++z) mass += a.box ? 1.0 : exp(-(double)z * z * a.inv2s2);
   a.eta_thr = (float)(1e-6 * mass * mass);
-  // BF16 tensor-core kernel for S <= 16 when asked for; otherwise the FP32 FIR kernel
-  const bool mma = tile == NYF_TILE_TENSOR && S <= 16;
+  // BF16 tensor-core kernel (n <= 3, S <= 16) when asked for; otherwise the FP32 FIR kernel
+  const bool mma = tile == NYF_TILE_TENSOR && !bf16 && conv_tc_supported(S, n);
   a.narrow = tile == NYF_TILE_NARROW ? 1 : 0;
-  const bool split = mma ? conv_mma_split(n) : n + 1 > conv_nq(Sc);
+  const bool split = mma ? false : n + 1 > conv_nq(Sc);
   a.out = split ? nullptr : out;
   a.zeta = split ? zeta_ws : nullptr;
   a.eta = eta_out;
   a.cout = cout;
   cudaError_t e;
-  if (mma) e = conv_mma_dispatch(a, st);
+  if (mma) e = conv_tc_dispatch(a, st);
   else if (Sc <= 8) e = conv_dispatch_a(Sc, a, st);
   else if (Sc <= 16) e = conv_dispatch_b(Sc, a, st);
   else e = conv_dispatch_c(Sc, a, st);

@@ -15,8 +15,10 @@ constexpr uint32_t kWaitLimit = 1u << 22;   // mbarrier polls before giving up
 __host__ __device__ inline float st_a(int m, int k) { return (float)(((m * 3 + k * 5) % 17) - 8) * 0.125f; }
 __host__ __device__ inline float st_b(int n, int k) { return (float)(((n * 7 + k * 3) % 13) - 6) * 0.25f; }
 
+// a_in_tmem: A is written into tensor memory (row m = lane m, bf16 pairs per
+// 32-bit column) instead of shared memory.
 __global__ void __launch_bounds__(128, 1) k_umma_selftest(float* __restrict__ D, int N, int K,
-                                                         int* __restrict__ status) {
+                                                         int a_in_tmem, int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_slot;
@@ -34,7 +36,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_selftest(float* __restrict__ D,
   }
   umma::fence_async_smem();
   uint32_t ncols = 32;
-  while ((int)ncols < N) ncols <<= 1;
+  while ((int)ncols < N + (a_in_tmem ? K / 2 : 0)) ncols <<= 1;
   if (warp == 0) umma::tmem_alloc(&tmem_slot, ncols);
   if (tid == 0) {
     umma::mbar_init(&mbar, 1);
@@ -44,15 +46,37 @@ __global__ void __launch_bounds__(128, 1) k_umma_selftest(float* __restrict__ D,
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tbase = tmem_slot;
+  const uint32_t acol = (uint32_t)N;                 // A's columns follow D's when in TMEM
+  if (a_in_tmem) {                                   // row m = 32 warp + lane, pairs of K
+    const int m = 32 * warp + lane;
+    for (int c0 = 0; c0 < K / 2; c0 += 32) {
+      float v[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int kk = 2 * (c0 + i);
+        __nv_bfloat162 h = __floats2bfloat162_rn(kk < K ? st_a(m, kk) : 0.f, kk + 1 < K ? st_a(m, kk + 1) : 0.f);
+        v[i] = __uint_as_float(*reinterpret_cast<uint32_t*>(&h));
+      }
+      umma::tmem_st32(tbase + ((uint32_t)(32 * warp) << 16) + acol + c0, v);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+  }
   if (tid == 0) {
     const uint32_t a0 = umma::smem_u32(A), b0 = umma::smem_u32(B);
     const uint32_t sbo = (uint32_t)K * 16;
-    for (int ks = 0; ks < K / 16; ++ks)
-      umma::mma_bf16(tbase, umma::sdesc(a0 + ks * 256, 128, sbo), umma::sdesc(b0 + ks * 256, 128, sbo),
-                     umma::idesc_bf16(M, N), ks > 0 ? 1u : 0u);
+    for (int ks = 0; ks < K / 16; ++ks) {
+      if (a_in_tmem)
+        umma::mma_bf16_ta(tbase, tbase + acol + 8 * ks, umma::sdesc(b0 + ks * 256, 128, sbo),
+                          umma::idesc_bf16(M, N), ks > 0 ? 1u : 0u);
+      else
+        umma::mma_bf16(tbase, umma::sdesc(a0 + ks * 256, 128, sbo), umma::sdesc(b0 + ks * 256, 128, sbo),
+                       umma::idesc_bf16(M, N), ks > 0 ? 1u : 0u);
+    }
     umma::commit(&mbar);
   }
-  const bool ok = umma::mbar_wait(&mbar, 0, kWaitLimit);
+  const bool ok = __all_sync(0xffffffffu, umma::mbar_wait(&mbar, 0, kWaitLimit));   // warp-uniform
   umma::fence_after_sync();
   if (!ok && lane == 0) atomicExch(status, 1);
   if (ok) {
@@ -75,8 +99,10 @@ __global__ void __launch_bounds__(128, 1) k_umma_selftest(float* __restrict__ D,
 
 using namespace nyf;
 
-extern "C" nyf_status nyf_selftest_umma(float* D, int N, int K, int* status, void* stream) {
-  if (!D || !status || N < 16 || N > 256 || (N & 15) || K < 16 || K > 128 || (K & 15))
+extern "C" nyf_status nyf_selftest_umma(float* D, int N, int K, int a_in_tmem, int* status,
+                                        void* stream) {
+  if (!D || !status || N < 16 || N > 256 || (N & 15) || K < 16 || K > 128 || (K & 15) ||
+      (a_in_tmem && N + K / 2 > 512))
     return NYF_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t smem = (size_t)(128 + N) * K * 2;
@@ -84,7 +110,7 @@ extern "C" nyf_status nyf_selftest_umma(float* D, int N, int K, int* status, voi
       cudaSuccess)
     return NYF_ERR_CUDA;
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return NYF_ERR_CUDA;
-  k_umma_selftest<<<1, 128, smem, st>>>(D, N, K, status);
+  k_umma_selftest<<<1, 128, smem, st>>>(D, N, K, a_in_tmem, status);
   count_launches(1);
   return cudaGetLastError() == cudaSuccess ? NYF_OK : NYF_ERR_CUDA;
 }

@@ -31,11 +31,12 @@ def operands(N, K):
     return A, B
 
 
+@pytest.mark.parametrize("a_in_tmem", [0, 1])
 @pytest.mark.parametrize("N,K", [(16, 16), (64, 32), (96, 160 // 2), (128, 128), (256, 64)])
-def test_tcgen05_gemm(lib, N, K):
+def test_tcgen05_gemm(lib, N, K, a_in_tmem):
     D = torch.full((128, N), float("nan"), dtype=torch.float32, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    rc = lib.nyf_selftest_umma(C.c_void_p(D.data_ptr()), N, K, C.c_void_p(status.data_ptr()),
+    rc = lib.nyf_selftest_umma(C.c_void_p(D.data_ptr()), N, K, a_in_tmem, C.c_void_p(status.data_ptr()),
                                C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 0
     torch.cuda.synchronize()
@@ -44,5 +45,5 @@ def test_tcgen05_gemm(lib, N, K):
     want = A @ B.T
     got = D.cpu().numpy().astype(np.float64)
     err = np.abs(got - want).max()
-    print(f"[parity] tcgen05 128x{N}x{K}: max abs err {err:.2e}")
+    print(f"[parity] tcgen05 128x{N}x{K} (A in {'TMEM' if a_in_tmem else 'smem'}): max abs err {err:.2e}")
     assert err <= 1e-5 * max(1.0, np.abs(want).max())
