@@ -236,13 +236,13 @@ def timed_steps(step, steps, flush, stream, lib):
     return float(np.mean(step_ms)), means
 
 
-def batched_extra(nyf, steps, warmup, flush, stream):
-    """The 64-image workload (BF16, K = 16): forward + backward by CUDA-graph replay."""
+def batched_extra(nyf, steps, warmup, flush, stream, precision="bf16"):
+    """The 64-image workload (K = 16): forward + backward by CUDA-graph replay."""
     import torch
     from paper_1901_06112_gb300 import synth
     batch = synth.batched_blf()
     shapes = [(w.H, w.W) for w in batch]
-    P = nyf.Params(K=16, kmeans_iters=10, precision="bf16")
+    P = nyf.Params(K=16, kmeans_iters=10, precision=precision)
     bt = nyf.Batched(shapes, [w.sigma_s for w in batch], [w.sigma_r for w in batch], P)
     f = bt.pack([w.f for w in batch])
     G = torch.randn(f.shape, generator=torch.Generator().manual_seed(0)).cuda()
@@ -262,7 +262,7 @@ def batched_extra(nyf, steps, warmup, flush, stream):
         ms.append(e0.elapsed_time(e1))
     mpix = bt.total / 3 / 1e6
     t = float(np.mean(ms))
-    return {"workload": "batched_blf_64_images_128-1024_K16_bf16", "images": len(batch),
+    return {"workload": f"batched_blf_64_images_128-1024_K16_{precision}", "images": len(batch),
             "megapixels": mpix, "ms_per_step": t, "value": mpix / (t / 1e3),
             "unit": "megapixels/s", "mode": "fwd+bwd, one CUDA-graph replay per step"}
 
@@ -378,10 +378,11 @@ def main():
                               lib)
         extras[other] = {"fwdbwd_value" if fwdbwd else "value": mp / (o_ms / 1e3),
                          "fwd_value": mp / (f_ms / 1e3), "unit": "megapixels/s"}
-        try:
-            extras["batched"] = batched_extra(nyf, max(3, args.steps // 4), 2, flush, stream)
-        except Exception as ex:                   # the side measurement must not hide the main one
-            extras["batched"] = {"error": str(ex)[:300]}
+        for prec, key in (("bf16", "batched"), ("fp32", "batched_fp32")):
+            try:
+                extras[key] = batched_extra(nyf, max(3, args.steps // 4), 2, flush, stream, prec)
+            except Exception as ex:               # the side measurement must not hide the main one
+                extras[key] = {"error": str(ex)[:300]}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
