@@ -56,10 +56,20 @@ def parse():
 
 CPU_SAMPLE = (192, 192)     # crop of the workload the oracle filters (and differentiates) per step
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the FP32 kernels on the
-# 1920 x 1080, K = 32 workload, from the ncu capture summarised in
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the convolution kernels
+# on the 1920 x 1080, K = 32 workload, from the ncu captures summarised in
 # profiles/ncu_conv_kernels_colour_blf_1920x1080.md; only for the kernels as captured.
-NCU_TRAFFIC = {}     # kernels changed since the last capture: traffic is reported as null
+NCU_TRAFFIC = {("conv_bwd", "fp32"): 1.420e9 + 0.253e9, ("conv_bwd", "bf16"): 1.420e9 + 0.253e9,
+               ("conv_combine", "fp32"): 0.323e9 + 1.035e9, ("conv_combine", "bf16"): 0.315e9 + 1.034e9}
+
+
+def bf16_tensor_peak():
+    """Dense BF16 tensor peak (TFLOP/s, burst) measured on this machine type, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback"
 
 
 def _oracle_step_code(h, w, backward):
@@ -348,14 +358,20 @@ def main():
     fwd_flops = conv_flops_per_pixel(planes, n, P.radius) * H * W
     bwd_flops = conv_bwd_flops_per_pixel(planes, n, P.radius) * H * W
 
-    captured = args.precision == "fp32" and (H, W, wl.K) == (1080, 1920, 32)
+    captured = (H, W, wl.K) == (1080, 1920, 32)
 
     def roof(name, flops, ms_k):
         a = flops / (ms_k / 1e3) / 1e12
-        return {"kernel": name, "bound": "alu" if args.precision == "fp32" or name != "conv_combine"
-                else "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
-                "traffic": NCU_TRAFFIC.get(name) if captured else None, "launch_ms": ms_k,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FP32 ALU)"}
+        tensor = args.precision == "bf16" and name == "conv_combine"   # the tcgen05 kernel
+        if tensor:
+            pk, how = bf16_tensor_peak()
+            basis = f"dense BF16 tensor peak, burst ({how}); FLOPs = the FIR's algorithmic count"
+        else:
+            pk, basis = peak, "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (FP32 ALU)"
+        return {"kernel": name, "bound": "tensor" if tensor else "alu", "achieved": a, "peak": pk,
+                "unit": "TFLOP/s", "frac": a / pk,
+                "traffic": NCU_TRAFFIC.get((name, args.precision)) if captured else None,
+                "launch_ms": ms_k, "peak_basis": basis}
 
     roof_fwd = roof("conv_combine", fwd_flops, stage_mean[3])
     roof_bwd = roof("conv_bwd", bwd_flops, stage_mean[4]) if fwdbwd else None
