@@ -124,8 +124,15 @@ def spectral_step(mu: np.ndarray, sigma_r: float, tau: float):
 
 
 def nystrom_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_r: float,
-                   taps: np.ndarray, tau: float, return_parts: bool = False):
-    """Algorithm 1 on the whole image.  f: H x W x n, p: H x W x rho, mu: m0 x rho."""
+                   taps: np.ndarray, tau: float, return_parts: bool = False, conv=None):
+    """Algorithm 1 on the whole image.  f: H x W x n, p: H x W x rho, mu: m0 x rho.
+
+    `conv`, if given, is the spatial filter omega * (.) on H x W (x c) arrays
+    (any linear operator, e.g. the recursive Gaussian of ``oracle.iir``); by
+    default it is ``conv_same`` with `taps`.
+    """
+    if conv is None:
+        conv = lambda a: conv_same(a, taps)
     f = np.asarray(f, np.float64)
     p = np.asarray(p, np.float64)
     H, W, n = f.shape
@@ -140,8 +147,8 @@ def nystrom_filter(f: np.ndarray, p: np.ndarray, mu: np.ndarray, sigma_r: float,
         v = extrapolate(B, Wv[:, k], alpha[k])       # Eq. (12)
         d = v.reshape(H, W)                          # d_k(x) = v_k(iota(x))
         h = d[..., None] * f                         # h_k(x) = d_k(x) f(x)
-        zeta += alpha[k] * d[..., None] * conv_same(h, taps)
-        eta += alpha[k] * d * conv_same(d, taps)
+        zeta += alpha[k] * d[..., None] * conv(h)
+        eta += alpha[k] * d * conv(d)
     g_hat = zeta / eta[..., None]
     if return_parts:
         return g_hat, dict(zeta=zeta, eta=eta, alpha=alpha, W=Wv, keep=keep)
