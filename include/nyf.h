@@ -25,7 +25,11 @@
  *    the paper's theta, Sec. IV setup).  Spatial kernel omega(z) =
  *    exp(-||z||^2 / (2 sigma_s^2)) on the window ||z||_inf <= S (S defaults to
  *    ceil(3 sigma_s), Sec. IV setup) or a box of ones; the window is clipped
- *    to the image (zero padding).
+ *    to the image (zero padding).  NYF_GAUSSIAN_IIR replaces the window by
+ *    the recursive Gaussian of Young & van Vliet (1995), the O(1) filter the
+ *    paper's experiments use (Sec. IV): a third-order causal recursion and
+ *    the same recursion run backwards, along columns and then rows, applied
+ *    to the zero-padded image (unit DC gain, no truncation radius).
  *  - Eq. (12) divides by the eigenvalues alpha_k of A; only modes with
  *    alpha_k > eig_rel_tol * alpha_max are used (their number is the rank r).
  */
@@ -55,7 +59,10 @@ typedef enum {
 } nyf_status;
 
 typedef enum { NYF_FP32 = 0, NYF_BF16 = 1 } nyf_precision;
-typedef enum { NYF_GAUSSIAN = 0, NYF_BOX = 1 } nyf_spatial;
+/* NYF_GAUSSIAN_IIR: forward only, NYF_FP32 only (the separable passes keep a
+ * K (n+1)-plane float32 intermediate in the workspace), 0.5 <= sigma_s <= 1e4,
+ * H and W <= 2016 (NYF_ERR_UNSUPPORTED otherwise); S and conv_tile are ignored. */
+typedef enum { NYF_GAUSSIAN = 0, NYF_BOX = 1, NYF_GAUSSIAN_IIR = 2 } nyf_spatial;
 
 /* Convolution kernel variant (nyf_params.conv_tile).  AUTO: tensor cores for
  * NYF_BF16, wide FP32 tiles otherwise.  WIDE / NARROW: FP32 FIR kernel with

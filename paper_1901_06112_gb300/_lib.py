@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "NYF_OK", 1: "NYF_ERR_INVALID_ARG", 2: "NYF_ERR_UNSUPPORTED",
                 3: "NYF_ERR_WORKSPACE", 4: "NYF_ERR_NUMERIC", 5: "NYF_ERR_CUDA",
                 6: "NYF_ERR_TIMEOUT"}
 FP32, BF16 = 0, 1
-GAUSSIAN, BOX = 0, 1
+GAUSSIAN, BOX, GAUSSIAN_IIR = 0, 1, 2
 TILE_AUTO, TILE_WIDE, TILE_NARROW, TILE_TENSOR = 0, 1, 2, 3
 MAX_K, MAX_RHO, MAX_S, MAX_CHANNELS = 64, 160, 32, 64
 

@@ -50,6 +50,7 @@ WsLayout ws_layout(const WsShape& s) {
   L.gw = take(s.bwd ? sizeof(double) * (2 * K * K + K) : 0);
   L.adj = take(s.bwd ? sizeof(float) * nq1 * N : 0);
   L.cbuf = take(s.bwd ? sizeof(float) * K * nq1 * N : 0);
+  L.ybuf = take(s.iir ? sizeof(float) * K * nq1 * N : 0);
   L.total = o;
   return L;
 }
@@ -114,18 +115,25 @@ nyf_status check_params(const nyf_params* p, int n) {
   if (p->kmeans_iters < 0) return NYF_ERR_INVALID_ARG;
   if (!(p->eig_rel_tol >= 0.0) || !isfinite(p->eig_rel_tol)) return NYF_ERR_INVALID_ARG;
   if (p->precision != NYF_FP32 && p->precision != NYF_BF16) return NYF_ERR_INVALID_ARG;
-  if (p->spatial != NYF_GAUSSIAN && p->spatial != NYF_BOX) return NYF_ERR_INVALID_ARG;
+  if (p->spatial != NYF_GAUSSIAN && p->spatial != NYF_BOX && p->spatial != NYF_GAUSSIAN_IIR)
+    return NYF_ERR_INVALID_ARG;
   if (p->spatial == NYF_GAUSSIAN && (!(p->sigma_s > 0.f) || !isfinite(p->sigma_s)))
     return NYF_ERR_INVALID_ARG;
+  if (p->spatial == NYF_GAUSSIAN_IIR) {
+    if (!(p->sigma_s >= 0.5f) || !isfinite(p->sigma_s)) return NYF_ERR_INVALID_ARG;
+    if (p->sigma_s > 1e4f || p->precision != NYF_FP32 || p->save_for_backward)
+      return NYF_ERR_UNSUPPORTED;
+  }
   if (p->spatial == NYF_BOX && p->S <= 0 && (!(p->sigma_s > 0.f) || !isfinite(p->sigma_s)))
     return NYF_ERR_INVALID_ARG;
   if (!(p->sample_frac > 0.f) || p->sample_frac > 1.f) return NYF_ERR_INVALID_ARG;
   if (n < 1 || n > NYF_MAX_CHANNELS) return NYF_ERR_INVALID_ARG;
+  if (p->patch_radius < 0) return NYF_ERR_INVALID_ARG;
+  if (p->conv_tile < NYF_TILE_AUTO || p->conv_tile > NYF_TILE_TENSOR) return NYF_ERR_INVALID_ARG;
+  if (p->spatial == NYF_GAUSSIAN_IIR) return NYF_OK;   // no window radius
   const int S = window_radius(p);
   if (S < 1) return NYF_ERR_INVALID_ARG;
   if (S > NYF_MAX_S) return NYF_ERR_UNSUPPORTED;
-  if (p->patch_radius < 0) return NYF_ERR_INVALID_ARG;
-  if (p->conv_tile < NYF_TILE_AUTO || p->conv_tile > NYF_TILE_TENSOR) return NYF_ERR_INVALID_ARG;
   return NYF_OK;
 }
 
@@ -154,6 +162,7 @@ nyf_status check_filter(const float* f, int H, int W, int n, int rho, const nyf_
   if (H < 1 || W < 1 || (int64_t)H * W > ((int64_t)1 << 31)) return NYF_ERR_INVALID_ARG;
   if (rho < 1 || rho > NYF_MAX_RHO) return NYF_ERR_INVALID_ARG;
   if (kmeans_smem_bytes(p->K, rho) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
+  if (p->spatial == NYF_GAUSSIAN_IIR && !iir_supported(H, W, n)) return NYF_ERR_UNSUPPORTED;
   return NYF_OK;
 }
 
@@ -169,7 +178,22 @@ WsShape shape_for(int H, int W, int n, int rho, const nyf_params* p) {
   s.bf16 = false;   // the filters keep phi in float32 (see nyf_params.precision)
   s.gather = p->patch_radius > 0;
   s.bwd = p->save_for_backward != 0 && p->patch_radius == 0;
+  s.iir = p->spatial == NYF_GAUSSIAN_IIR;
   return s;
+}
+
+// Spatial convolutions + combine (Eqs. (14)-(15)): the recursive Gaussian or the FIR window.
+cudaError_t spatial_combine(const float* f, int H, int W, int n, const nyf_params* p, int tile,
+                            char* w, const WsLayout& L, float* out, float* cout, cudaStream_t st) {
+  DevState* state = reinterpret_cast<DevState*>(w + L.state);
+  if (p->spatial == NYF_GAUSSIAN_IIR)
+    return launch_iir_combine(f, H, W, n, reinterpret_cast<const float*>(w + L.phi), p->K,
+                              p->sigma_s, state, out, reinterpret_cast<float*>(w + L.eta),
+                              reinterpret_cast<float*>(w + L.zeta),
+                              reinterpret_cast<float*>(w + L.ybuf), st);
+  return launch_conv_combine(f, H, W, n, w + L.phi, false, tile, p->spatial, p->sigma_s,
+                             window_radius(p), state, out, reinterpret_cast<float*>(w + L.eta),
+                             reinterpret_cast<float*>(w + L.zeta), cout, st);
 }
 
 // Landmarks into ws: copied, or k-means on the rows X (N x rho).
@@ -247,11 +271,8 @@ nyf_status blf_impl(const float* f, const float* guide, int H, int W, int n, int
   }
   {
     Stage t(st, 3, timed);
-    NYF_TRY(launch_conv_combine(f, H, W, n, phi, false, tile, p->spatial, p->sigma_s, window_radius(p),
-                                state, out, reinterpret_cast<float*>(w + L.eta),
-                                reinterpret_cast<float*>(w + L.zeta),
-                                p->save_for_backward ? reinterpret_cast<float*>(w + L.cbuf) : nullptr,
-                                st));
+    NYF_TRY(spatial_combine(f, H, W, n, p, tile, w, L, out,
+                            p->save_for_backward ? reinterpret_cast<float*>(w + L.cbuf) : nullptr, st));
   }
   return NYF_OK;
 }
@@ -470,7 +491,7 @@ nyf_status nyf_kmeans(const float* X, int64_t N, int rho, int K, int iters, uint
       K < 1 || K > NYF_MAX_K || K > N || iters < 0)
     return NYF_ERR_INVALID_ARG;
   if (kmeans_smem_bytes(K, rho) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
-  WsShape s{(int)N, 1, N, 1, rho, K, N, false, false, false};
+  WsShape s{(int)N, 1, N, 1, rho, K, N, false, false, false, false};
   const WsLayout L = ws_layout(s);
   if (!ws_ok(ws, ws_bytes, L.km_qpart + sizeof(float) * kKmeansBlocks)) return NYF_ERR_WORKSPACE;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -493,7 +514,7 @@ nyf_status nyf_features(const float* guide, int64_t N, int rho, const float* lan
       !(eig_rel_tol >= 0.0) || (precision != NYF_FP32 && precision != NYF_BF16))
     return NYF_ERR_INVALID_ARG;
   if (sizeof(float) * ((size_t)K * rho + (size_t)K * K) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
-  WsShape s{(int)N, 1, N, 1, rho, K, N, precision == NYF_BF16, false, false};
+  WsShape s{(int)N, 1, N, 1, rho, K, N, precision == NYF_BF16, false, false, false};
   const WsLayout L = ws_layout(s);
   if (!ws_ok(ws, ws_bytes, L.eig + eig_scratch_bytes())) return NYF_ERR_WORKSPACE;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -553,9 +574,7 @@ nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params*
   }
   {
     Stage t(st, 3);
-    NYF_TRY(launch_conv_combine(f, H, W, n, phi, false, tile, p->spatial, p->sigma_s, window_radius(p),
-                                state, out, reinterpret_cast<float*>(w + L.eta),
-                                reinterpret_cast<float*>(w + L.zeta), nullptr, st));
+    NYF_TRY(spatial_combine(f, H, W, n, p, tile, w, L, out, nullptr, st));
   }
   return NYF_OK;
 }

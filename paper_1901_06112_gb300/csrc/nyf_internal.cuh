@@ -32,7 +32,7 @@ struct DevState {
 // Byte offsets of every region of a workspace (all 256-byte aligned).
 struct WsLayout {
   size_t state, landmarks, what, eig, init_idx, km_part, km_qpart, sample_idx, sample_x, phi,
-      eta, zeta, dphi, gpart, spart, gw, adj, cbuf, total;
+      eta, zeta, dphi, gpart, spart, gw, adj, cbuf, ybuf, total;
 };
 
 // Problem geometry used to size a workspace.
@@ -46,6 +46,7 @@ struct WsShape {
   bool bf16;        // features stored as bfloat16
   bool gather;      // k-means rows are gathered (subsample or NLM patches)
   bool bwd;         // regions of the backward pass (saved convolutions, adjoints, partials)
+  bool iir;         // recursive-Gaussian planes (omega_v * (phi_k f_c), K (n + 1) planes)
 };
 
 WsLayout ws_layout(const WsShape& s);
@@ -95,6 +96,10 @@ cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void*
                                 float* out, float* eta_out, float* zeta_ws, float* cout,
                                 cudaStream_t st);
 int conv_compiled_radius(int S);
+bool iir_supported(int H, int W, int n);
+cudaError_t launch_iir_combine(const float* f, int H, int W, int n, const float* phi, int K,
+                               float sigma_s, DevState* state, float* out, float* eta_out,
+                               float* zeta_ws, float* ybuf, cudaStream_t st);
 bool conv_split(int S, int n);
 cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spatial, float sigma_s,
                             int S, const void* phi, bool bf16, const float* eta, const float* out,

@@ -27,7 +27,7 @@ class Params:
     seed: int = 0
     eig_rel_tol: float = 1e-7
     precision: str = "fp32"        # "fp32" | "bf16": storage of the per-pixel features
-    spatial: str = "gaussian"      # "gaussian" | "box"
+    spatial: str = "gaussian"      # "gaussian" | "box" | "gaussian_iir" (recursive, Sec. IV)
     S: int = 0                     # window radius; 0 -> ceil(3 sigma_s)
     patch_radius: int = 0          # NLM patch radius
     sample_frac: float = 1.0
@@ -39,7 +39,8 @@ class Params:
                            int(self.kmeans_iters), int(self.seed) & ((1 << 64) - 1),
                            float(self.eig_rel_tol),
                            L.BF16 if self.precision == "bf16" else L.FP32,
-                           L.BOX if self.spatial == "box" else L.GAUSSIAN, int(self.S),
+                           {"gaussian": L.GAUSSIAN, "box": L.BOX,
+                            "gaussian_iir": L.GAUSSIAN_IIR}[self.spatial], int(self.S),
                            int(self.patch_radius), float(self.sample_frac),
                            {"auto": L.TILE_AUTO, "wide": L.TILE_WIDE, "narrow": L.TILE_NARROW,
                             "tensor": L.TILE_TENSOR}[self.conv_tile],

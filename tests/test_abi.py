@@ -85,3 +85,31 @@ def test_batched_workspace_is_the_sum_of_aligned_slices(lib):
     assert total == want
     items[1].H = 0
     assert lib.nyf_batched_workspace_size(items, 3, 3, C.byref(p)) == 0
+
+
+def test_recursive_gaussian_host_checks(lib):
+    # spatial = NYF_GAUSSIAN_IIR (2): no window radius, a K (n + 1)-plane intermediate
+    fir = _lib.NyfParams(3.0, 30.0, 8, 10, 0, 1e-7, 0, 0, 0, 0, 1.0, 0)
+    iir = _lib.NyfParams(3.0, 30.0, 8, 10, 0, 1e-7, 0, 2, 0, 0, 1.0, 0)
+    s_fir = lib.nyf_workspace_size(256, 200, 3, 3, C.byref(fir))
+    s_iir = lib.nyf_workspace_size(256, 200, 3, 3, C.byref(iir))
+    assert s_iir >= s_fir + 4 * 8 * 4 * 256 * 200
+    bad = C.c_void_p(256)
+    # sigma_s of 20 has no FIR window (S = 60 > NYF_MAX_S) but is fine recursively:
+    # the call gets as far as the workspace check
+    big = _lib.NyfParams(20.0, 30.0, 8, 10, 0, 1e-7, 0, 2, 0, 0, 1.0, 0)
+    assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(big), None, bad, bad, 16, None) == 3
+    big.spatial = 0
+    assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(big), None, bad, bad, 16, None) == 2
+    small = _lib.NyfParams(0.4, 30.0, 8, 10, 0, 1e-7, 0, 2, 0, 0, 1.0, 0)
+    assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(small), None, bad, bad, 16, None) == 1
+    bf16 = _lib.NyfParams(3.0, 30.0, 8, 10, 0, 1e-7, 1, 2, 0, 0, 1.0, 0)
+    assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(bf16), None, bad, bad, 16, None) == 2
+    saving = _lib.NyfParams(3.0, 30.0, 8, 10, 0, 1e-7, 0, 2, 0, 0, 1.0, 0)
+    saving.save_for_backward = 1
+    assert lib.nyf_filter_blf(bad, None, 8, 8, 3, 3, C.byref(saving), None, bad, bad, 16, None) == 2
+    # lines longer than 32 lanes x 63 values are not implemented
+    assert lib.nyf_filter_blf(bad, None, 2017, 8, 3, 3, C.byref(iir), None, bad, bad, 16, None) == 2
+    assert lib.nyf_filter_blf(bad, None, 8, 2017, 3, 3, C.byref(iir), None, bad, bad, 16, None) == 2
+    assert lib.nyf_filter_blf(bad, None, 2016, 2016, 3, 3, C.byref(iir), None, bad, bad, 16,
+                              None) == 3
