@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--mode", default="fwdbwd", choices=["fwd", "fwdbwd"])
+    ap.add_argument("--spatial", default="gaussian", choices=["gaussian", "gaussian_iir"],
+                    help="omega: truncated FIR Gaussian, or the recursive Gaussian (forward, fp32)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the forward-only, BF16 and batched side measurements")
     ap.add_argument("--impl", default="nyf", choices=["nyf", "reference"])
@@ -61,6 +63,22 @@ CPU_SAMPLE = (192, 192)     # crop of the workload the oracle filters (and diffe
 # profiles/ncu_conv_kernels_colour_blf_1920x1080.md; only for the kernels as captured.
 NCU_TRAFFIC = {("conv_bwd", "fp32"): 1.420e9 + 0.253e9, ("conv_bwd", "bf16"): 1.420e9 + 0.253e9,
                ("conv_combine", "fp32"): 0.323e9 + 1.035e9, ("conv_combine", "bf16"): 0.315e9 + 1.034e9}
+
+
+def hbm_peak():
+    """Measured copy bandwidth (GB/s) on this machine type, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def iir_bytes_per_pixel(K, n):
+    """Algorithmic DRAM bytes per pixel of the two recursive-Gaussian passes:
+    column pass reads phi (4 K) and f (4 n), writes the K (n + 1) planes Y;
+    row pass reads Y and phi, writes g_hat (4 n) and eta (4)."""
+    return 4 * K + 4 * n + 4 * K * (n + 1) + 4 * K * (n + 1) + 4 * K + 4 * n + 4
 
 
 def bf16_tensor_peak():
@@ -277,6 +295,36 @@ def batched_extra(nyf, steps, warmup, flush, stream, precision="bf16"):
             "unit": "megapixels/s", "mode": "fwd+bwd, one CUDA-graph replay per step"}
 
 
+def iir_extra(nyf, lib, f_dev, wl, steps, flush, stream):
+    """The same workload with the recursive Gaussian (Young & van Vliet, Sec. IV) as
+    omega: forward only, FP32; the two passes are HBM-bound."""
+    H, W, n = wl.f.shape
+    P = nyf.Params(sigma_s=wl.sigma_s, sigma_r=wl.sigma_r, K=wl.K, kmeans_iters=wl.kmeans_iters,
+                   seed=wl.seed, spatial="gaussian_iir")
+    ws = nyf.make_workspace(H, W, n, n, P)
+    out = f_dev.new_empty(f_dev.shape)
+
+    def step():
+        nyf.blf(f_dev, P, out=out, ws=ws)
+    lib.nyf_set_timing(1)
+    for _ in range(3):
+        step()
+    ms, stages = timed_steps(step, steps, flush, stream, lib)
+    lib.nyf_set_timing(0)
+    st = nyf.stats(ws)
+    planes = wl.K if st["rank"] > 0 else 0
+    gb = iir_bytes_per_pixel(planes, n) * H * W / 1e9
+    pk, how = hbm_peak()
+    a = gb / (stages[3] / 1e3)
+    return {"workload": wl.name + "_recursive_gaussian", "value": H * W / 1e6 / (ms / 1e3),
+            "ms_per_step": ms, "unit": "megapixels/s", "mode": "fwd", "precision": "fp32",
+            "status": st["status"], "conv_ms": stages[3],
+            "roofline": {"kernel": "k_cols + k_rows (both passes)", "bound": "hbm",
+                         "achieved": a, "peak": pk, "unit": "GB/s", "frac": a / pk,
+                         "traffic": None, "algorithmic_GB": gb,
+                         "peak_basis": f"copy bandwidth ({how})"}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -301,11 +349,14 @@ def main():
     wl = synth.colour_blf_hd()
     H, W, n = wl.f.shape
     fwdbwd = args.mode == "fwdbwd"
+    iir = args.spatial == "gaussian_iir"
+    if iir and (fwdbwd or args.precision != "fp32"):
+        raise SystemExit("--spatial gaussian_iir runs the forward in fp32: add --mode fwd")
 
     def make(precision, bwd=False):
         return nyf.Params(sigma_s=wl.sigma_s, sigma_r=wl.sigma_r, K=wl.K,
                           kmeans_iters=wl.kmeans_iters, seed=wl.seed + rank, precision=precision,
-                          save_for_backward=bwd)
+                          save_for_backward=bwd, spatial=args.spatial)
 
     P = make(args.precision, fwdbwd)
     f_dev = torch.from_numpy(wl.f).to(dev)
@@ -374,6 +425,14 @@ def main():
                 "launch_ms": ms_k, "peak_basis": basis}
 
     roof_fwd = roof("conv_combine", fwd_flops, stage_mean[3])
+    if iir:
+        gb = iir_bytes_per_pixel(planes, n) * H * W / 1e9
+        pk_h, how_h = hbm_peak()
+        a_h = gb / (stage_mean[3] / 1e3)
+        roof_fwd = {"kernel": "k_cols + k_rows (both recursive passes)", "bound": "hbm",
+                    "achieved": a_h, "peak": pk_h, "unit": "GB/s", "frac": a_h / pk_h,
+                    "traffic": None, "launch_ms": stage_mean[3], "algorithmic_GB": gb,
+                    "peak_basis": f"copy bandwidth ({how_h})"}
     roof_bwd = roof("conv_bwd", bwd_flops, stage_mean[4]) if fwdbwd else None
     dominant = roof_bwd if (fwdbwd and stage_mean[4] > stage_mean[3]) else roof_fwd
 
@@ -386,19 +445,28 @@ def main():
             extras["fwd"] = {"value": mp / (fwd_ms / 1e3), "ms_per_step": fwd_ms,
                              "unit": "megapixels/s", "precision": args.precision}
         other = "bf16" if args.precision == "fp32" else "fp32"
-        Po = make(other, fwdbwd)
-        for _ in range(2):
-            make_step(Po, fwdbwd)()
-        o_ms, _ = timed_steps(make_step(Po, fwdbwd), max(3, args.steps // 2), flush, stream, lib)
-        f_ms, _ = timed_steps(make_step(make(other), False), max(3, args.steps // 2), flush, stream,
-                              lib)
-        extras[other] = {"fwdbwd_value" if fwdbwd else "value": mp / (o_ms / 1e3),
-                         "fwd_value": mp / (f_ms / 1e3), "unit": "megapixels/s"}
+        if iir:
+            other = None
+        if other:
+            Po = make(other, fwdbwd)
+            for _ in range(2):
+                make_step(Po, fwdbwd)()
+            o_ms, _ = timed_steps(make_step(Po, fwdbwd), max(3, args.steps // 2), flush, stream, lib)
+            f_ms, _ = timed_steps(make_step(make(other), False), max(3, args.steps // 2), flush,
+                                  stream, lib)
+            extras[other] = {"fwdbwd_value" if fwdbwd else "value": mp / (o_ms / 1e3),
+                             "fwd_value": mp / (f_ms / 1e3), "unit": "megapixels/s"}
         for prec, key in (("bf16", "batched"), ("fp32", "batched_fp32")):
             try:
                 extras[key] = batched_extra(nyf, max(3, args.steps // 4), 2, flush, stream, prec)
             except Exception as ex:               # the side measurement must not hide the main one
                 extras[key] = {"error": str(ex)[:300]}
+        if not iir:
+            try:
+                extras["recursive_gaussian"] = iir_extra(nyf, lib, f_dev, wl,
+                                                         max(3, args.steps // 2), flush, stream)
+            except Exception as ex:
+                extras["recursive_gaussian"] = {"error": str(ex)[:300]}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -435,7 +503,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": wl.name, "H": H, "W": W, "n": n, "sigma_s": wl.sigma_s,
                        "sigma_r": wl.sigma_r, "K": wl.K, "kmeans_iters": wl.kmeans_iters,
-                       "precision": args.precision,
+                       "precision": args.precision, "spatial": args.spatial,
                        "mode": "fwd+bwd" if fwdbwd else "fwd", "rank_r": r,
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{world}"},
