@@ -325,6 +325,42 @@ def iir_extra(nyf, lib, f_dev, wl, steps, flush, stream):
                          "peak_basis": f"copy bandwidth ({how})"}}
 
 
+def pca_nlm_extra(nyf, steps, flush, stream):
+    """PCA-NLM at the paper's parameters (Sec. IV): 768 x 512 colour, 7x7x3 patches projected
+    on 25 principal directions, K = 31, 21 x 21 box; the whole call (patch PCA, projection,
+    k-means, eig, features, convolutions) per step."""
+    import torch
+    from paper_1901_06112_gb300 import synth
+    w = synth.colour_pca_nlm()
+    f = torch.from_numpy(w.f).cuda()
+    P = nyf.Params(sigma_r=w.sigma_r, K=w.K, spatial="box", S=w.S, patch_radius=w.patch_radius,
+                   sample_frac=w.sample_frac, seed=w.seed)
+    ws = nyf.make_pca_workspace(w.H, w.W, 3, w.pca_dim, P)
+    out = torch.empty_like(f)
+    for _ in range(3):
+        nyf.pca_nlm(f, w.pca_dim, P, out=out, ws=ws)
+    torch.cuda.synchronize()
+
+    def t(fn):
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.mean(ms))
+    ms = t(lambda: nyf.pca_nlm(f, w.pca_dim, P, out=out, ws=ws))
+    st = nyf.stats(ws)
+    pca_ms = t(lambda: nyf.patch_pca(f, w.patch_radius, w.pca_dim))
+    return {"workload": w.name, "value": w.H * w.W / 1e6 / (ms / 1e3), "ms_per_step": ms,
+            "unit": "megapixels/s", "mode": "fwd", "patch_pca_ms": pca_ms, "status": st["status"],
+            "rank": st["rank"]}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -467,6 +503,10 @@ def main():
                                                          max(3, args.steps // 2), flush, stream)
             except Exception as ex:
                 extras["recursive_gaussian"] = {"error": str(ex)[:300]}
+            try:
+                extras["pca_nlm"] = pca_nlm_extra(nyf, max(3, args.steps // 4), flush, stream)
+            except Exception as ex:
+                extras["pca_nlm"] = {"error": str(ex)[:300]}
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None

@@ -194,6 +194,48 @@ nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params*
                           const float* landmarks, float* out, void* ws, size_t ws_bytes,
                           void* stream);
 
+/* ---- PCA-NLM (Sec. IV: the paper's NLM experiments use principal-neighbourhood
+ * NLM).  The patch guide p(x) of nyf_filter_nlm (rho = n (2r+1)^2 <= 160, r =
+ * params->patch_radius >= 1) is replaced by its coordinates in the q leading
+ * principal directions of the image's patches:
+ *     m = (1/N) sum_x p(x),  C = (1/N) sum_x (p(x) - m)(p(x) - m)^T = U diag(lambda) U^T,
+ *     guide p~(x) = U_q^T (p(x) - m),   1 <= q <= min(rho, 32).
+ * The leading eigenvectors are unique only up to sign and rotations within
+ * groups of equal eigenvalues; the filter depends on U_q only through the
+ * subspace it spans. */
+
+/* Mean patch, all rho eigenvalues of C (descending) and the q leading
+ * eigenvectors.  Covariance accumulated in FP32 per CTA from patches shifted by
+ * the channel means, reduced in FP64; eigendecomposition by cyclic Jacobi in
+ * FP32 on one CTA (NYF_ERR_TIMEOUT latched in ws if it has not converged after
+ * 20 sweeps).
+ *   mean     rho floats (device, out)
+ *   basis    rho x q floats, row-major: basis[i * q + j] = component i of
+ *            eigenvector j (device, out)
+ *   eigvals  rho floats (device, out)
+ *   ws       at least nyf_patch_pca_workspace_size(n, r) bytes, 256-B aligned.
+ * NYF_ERR_INVALID_ARG for r < 1, rho > 160, q outside [1, min(rho, 32)]. */
+size_t nyf_patch_pca_workspace_size(int n, int r);
+nyf_status nyf_patch_pca(const float* f, int H, int W, int n, int r, int q, float* mean,
+                         float* basis, float* eigvals, void* ws, size_t ws_bytes, void* stream);
+
+/* guide (H x W x q, device, out) = U_q^T (p(x) - m) with the given mean and basis
+ * (layouts as for nyf_patch_pca).  No workspace. */
+nyf_status nyf_pca_project(const float* f, int H, int W, int n, int r, int q, const float* mean,
+                           const float* basis, float* guide, void* stream);
+
+/* PCA-NLM through Algorithm 1: the PCA guide (from mean and basis when both are
+ * given, else from the image's own moments), then the joint filter of
+ * nyf_filter_blf with that guide (rho = q): k-means on round(sample_frac * N)
+ * guide rows (landmarks == NULL) or the given q-dimensional landmarks, and
+ * params->spatial / S as for the other filters (the paper: a box, S = 10).
+ * params->save_for_backward must be 0 and precision FP32 or BF16 as for
+ * nyf_filter_blf.  ws: nyf_pca_nlm_workspace_size bytes. */
+size_t nyf_pca_nlm_workspace_size(int H, int W, int n, int q, const nyf_params* params);
+nyf_status nyf_filter_pca_nlm(const float* f, int H, int W, int n, int q, const nyf_params* params,
+                              const float* mean, const float* basis, const float* landmarks,
+                              float* out, void* ws, size_t ws_bytes, void* stream);
+
 /* Adjoint of nyf_filter_blf (the paper has no gradients; derived from
  * Eqs. (9)-(15)).  Must follow the nyf_filter_blf call that produced `out`
  * on the same workspace, with the same f, guide and params, and

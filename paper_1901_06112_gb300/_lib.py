@@ -74,6 +74,14 @@ _SIGNATURES.update({
                                                   _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "nyf_batched_stats": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(NyfParams), C.c_int,
                                     C.POINTER(NyfStats), _P]),
+    "nyf_patch_pca_workspace_size": (C.c_size_t, [C.c_int, C.c_int]),
+    "nyf_patch_pca": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P,
+                                C.c_size_t, _P]),
+    "nyf_pca_project": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P]),
+    "nyf_pca_nlm_workspace_size": (C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int,
+                                                C.POINTER(NyfParams)]),
+    "nyf_filter_pca_nlm": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(NyfParams),
+                                     _P, _P, _P, _P, _P, C.c_size_t, _P]),
 })
 
 _lib = None

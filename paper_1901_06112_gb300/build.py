@@ -15,7 +15,7 @@ LIB = os.path.join(PKG, "libnyf.so")
 SOURCES = ["api.cu", "kmeans.cu", "eig.cu", "features.cu", "conv.cu", "conv_a.cu", "conv_b.cu",
            "conv_c.cu", "backward.cu", "backward_a.cu", "backward_b.cu", "backward_c.cu",
            "noalloc.cu", "conv_tc.cu", "umma_selftest.cu", "iir.cu", "iir_cols_a.cu",
-           "iir_cols_b.cu", "iir_rows_a.cu", "iir_rows_b.cu"]
+           "iir_cols_b.cu", "iir_rows_a.cu", "iir_rows_b.cu", "pca.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE]

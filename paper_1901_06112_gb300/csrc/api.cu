@@ -234,7 +234,7 @@ namespace {
 
 nyf_status blf_impl(const float* f, const float* guide, int H, int W, int n, int rho,
                     const nyf_params* p, const float* landmarks, float* out, void* ws,
-                    size_t ws_bytes, void* stream, bool timed) {
+                    size_t ws_bytes, void* stream, bool timed, const int* pre_status = nullptr) {
   if (!p || p->patch_radius != 0) return NYF_ERR_INVALID_ARG;
   if (!guide) {
     if (rho != n) return NYF_ERR_INVALID_ARG;
@@ -251,6 +251,8 @@ nyf_status blf_impl(const float* f, const float* guide, int H, int W, int n, int
   const int64_t N = (int64_t)H * W;
   const int tile = resolve_tile(p);
   NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
+  if (pre_status)   // status of work done for this call before the filter (PCA guide)
+    NYF_TRY(cudaMemcpyAsync(&state->status, pre_status, sizeof(int), cudaMemcpyDeviceToDevice, st));
   if (timed) timing_begin(0, 3);
   {
     Stage t(st, 0, timed);
@@ -425,6 +427,45 @@ nyf_status run_batched(const nyf_batch_item* items, int B, int n, const nyf_para
       if (cudaStreamWaitEvent(caller, P->join[i], 0) != cudaSuccess) return NYF_ERR_CUDA;
     }
   return status;
+}
+
+
+// ---- PCA-NLM: the joint-filter layout for a q-dimensional guide, then the
+// guide, the PCA outputs, a device state for the eigendecomposition and its scratch.
+struct PcaLayout {
+  WsLayout blf;
+  size_t guide, mean, basis, eig, state, scratch, total;
+};
+
+PcaLayout pca_layout(int H, int W, int n, int q, const nyf_params* p) {
+  nyf_params p2 = *p;
+  p2.patch_radius = 0;
+  PcaLayout L;
+  L.blf = ws_layout(shape_for(H, W, n, q, &p2));
+  const int rho = nlm_rho(n, p->patch_radius);
+  size_t o = L.blf.total;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.guide = take(sizeof(float) * (size_t)H * W * q);
+  L.mean = take(sizeof(float) * rho);
+  L.basis = take(sizeof(float) * (size_t)rho * q);
+  L.eig = take(sizeof(float) * rho);
+  L.state = take(sizeof(DevState));
+  L.scratch = take(pca_scratch_bytes(n, p->patch_radius));
+  L.total = o;
+  return L;
+}
+
+nyf_status check_pca(int H, int W, int n, int r, int q) {
+  if (H < 1 || W < 1 || n < 1 || r < 1) return NYF_ERR_INVALID_ARG;
+  const int rho = nlm_rho(n, r);
+  if (rho > 160 || q < 1 || q > rho || q > 32) return NYF_ERR_INVALID_ARG;
+  if ((int64_t)H * W > ((int64_t)1 << 31)) return NYF_ERR_INVALID_ARG;
+  if (pca_jacobi_smem(rho) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
+  return NYF_OK;
 }
 
 }  // namespace
@@ -611,6 +652,75 @@ size_t nyf_batched_workspace_size(const nyf_batch_item* items, int B, int n,
   if (!items || B < 1 || !p) return 0;
   size_t total = 0;
   return batch_layout(items, B, n, p, nullptr, &total) ? total : 0;
+}
+
+size_t nyf_patch_pca_workspace_size(int n, int r) {
+  if (n < 1 || r < 1 || nlm_rho(n, r) > 160) return 0;
+  return align256(sizeof(DevState)) + pca_scratch_bytes(n, r);
+}
+
+nyf_status nyf_patch_pca(const float* f, int H, int W, int n, int r, int q, float* mean,
+                         float* basis, float* eigvals, void* ws, size_t ws_bytes, void* stream) {
+  nyf_status s = check_pca(H, W, n, r, q);
+  if (s != NYF_OK) return s;
+  if (!f || !mean || !basis || !eigvals || !aligned4(f)) return NYF_ERR_INVALID_ARG;
+  if (!ws_ok(ws, ws_bytes, nyf_patch_pca_workspace_size(n, r))) return NYF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  DevState* state = reinterpret_cast<DevState*>(w);
+  NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
+  NYF_TRY(launch_patch_pca(f, H, W, n, r, q, w + align256(sizeof(DevState)), mean, basis, eigvals,
+                           state, st));
+  return NYF_OK;
+}
+
+nyf_status nyf_pca_project(const float* f, int H, int W, int n, int r, int q, const float* mean,
+                           const float* basis, float* guide, void* stream) {
+  nyf_status s = check_pca(H, W, n, r, q);
+  if (s != NYF_OK) return s;
+  if (!f || !mean || !basis || !guide || !aligned4(f)) return NYF_ERR_INVALID_ARG;
+  NYF_TRY(launch_pca_project(f, H, W, n, r, q, mean, basis, guide,
+                             reinterpret_cast<cudaStream_t>(stream)));
+  return NYF_OK;
+}
+
+size_t nyf_pca_nlm_workspace_size(int H, int W, int n, int q, const nyf_params* p) {
+  if (!p || check_pca(H, W, n, p->patch_radius, q) != NYF_OK || p->K < 1 || p->K > NYF_MAX_K)
+    return 0;
+  if (!(p->sample_frac > 0.f) || p->sample_frac > 1.f) return 0;
+  return pca_layout(H, W, n, q, p).total;
+}
+
+nyf_status nyf_filter_pca_nlm(const float* f, int H, int W, int n, int q, const nyf_params* p,
+                              const float* mean, const float* basis, const float* landmarks,
+                              float* out, void* ws, size_t ws_bytes, void* stream) {
+  if (!p || p->save_for_backward) return NYF_ERR_INVALID_ARG;
+  nyf_status s = check_pca(H, W, n, p->patch_radius, q);
+  if (s != NYF_OK) return s;
+  if ((mean == nullptr) != (basis == nullptr)) return NYF_ERR_INVALID_ARG;
+  nyf_params p2 = *p;
+  p2.patch_radius = 0;
+  s = check_filter(f, H, W, n, q, &p2, out);
+  if (s != NYF_OK) return s;
+  const PcaLayout L = pca_layout(H, W, n, q, p);
+  if (!ws_ok(ws, ws_bytes, L.total)) return NYF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  const int r = p->patch_radius;
+  const int* pre = nullptr;
+  if (!basis) {
+    DevState* ps = reinterpret_cast<DevState*>(w + L.state);
+    NYF_TRY(cudaMemsetAsync(ps, 0, sizeof(DevState), st));
+    mean = reinterpret_cast<float*>(w + L.mean);
+    basis = reinterpret_cast<float*>(w + L.basis);
+    NYF_TRY(launch_patch_pca(f, H, W, n, r, q, w + L.scratch, reinterpret_cast<float*>(w + L.mean),
+                             reinterpret_cast<float*>(w + L.basis), reinterpret_cast<float*>(w + L.eig),
+                             ps, st));
+    pre = &ps->status;
+  }
+  float* guide = reinterpret_cast<float*>(w + L.guide);
+  NYF_TRY(launch_pca_project(f, H, W, n, r, q, mean, basis, guide, st));
+  return blf_impl(f, guide, H, W, n, q, &p2, landmarks, out, ws, L.blf.total, stream, true, pre);
 }
 
 nyf_status nyf_filter_blf_batched(const float* f, const nyf_batch_item* items, int B, int n,

@@ -111,6 +111,13 @@ cudaError_t launch_bwd_features(const float* f, const float* guide, int H, int W
                                 float* grad_guide, float* gpart, const float* spart, double* gw,
                                 const void* eig_scratch, float* grad_sigma, DevState* state,
                                 cudaStream_t st);
+size_t pca_scratch_bytes(int n, int r);
+size_t pca_jacobi_smem(int rho);
+cudaError_t launch_patch_pca(const float* f, int H, int W, int n, int r, int q, void* scratch,
+                             float* mean, float* basis, float* eigvals, DevState* state,
+                             cudaStream_t st);
+cudaError_t launch_pca_project(const float* f, int H, int W, int n, int r, int q, const float* mean,
+                               const float* basis, float* guide, cudaStream_t st);
 size_t backward_gpart_floats(int K);
 size_t backward_spart_floats(int H, int W, int n);
 const double* eig_A64(const void* scratch);

@@ -134,6 +134,65 @@ def nlm(f, params: Params, landmarks=None, out=None, ws: Workspace | None = None
     return out
 
 
+def patch_pca(f, r: int, q: int):
+    """PCA of the image's (2r+1)^2 n patches (PCA-NLM, Sec. IV): (mean, basis rho x q,
+    eigenvalues rho, descending, ws) -- the workspace holds the device status word."""
+    lib = L.load()
+    _check_image(f, "f")
+    H, W, n = f.shape
+    rho = n * (2 * r + 1) ** 2
+    mean = torch.empty(rho, dtype=torch.float32, device=f.device)
+    basis = torch.empty(rho, q, dtype=torch.float32, device=f.device)
+    lam = torch.empty(rho, dtype=torch.float32, device=f.device)
+    nb = lib.nyf_patch_pca_workspace_size(n, r)
+    if nb == 0:
+        raise ValueError("patch dimension outside 1..160")
+    ws = Workspace(nb, f.device)
+    L.check(lib.nyf_patch_pca(_ptr(f), H, W, n, r, q, _ptr(mean), _ptr(basis), _ptr(lam), ws.cptr(),
+                              ws.nbytes, _stream()), "nyf_patch_pca")
+    return mean, basis, lam, ws
+
+
+def pca_project(f, r: int, mean, basis):
+    """The H x W x q PCA guide U_q^T (p(x) - m)."""
+    lib = L.load()
+    _check_image(f, "f")
+    H, W, n = f.shape
+    q = basis.shape[1]
+    guide = torch.empty(H, W, q, dtype=torch.float32, device=f.device)
+    L.check(lib.nyf_pca_project(_ptr(f), H, W, n, r, q, _ptr(mean.contiguous()),
+                                _ptr(basis.contiguous()), _ptr(guide), _stream()), "nyf_pca_project")
+    return guide
+
+
+def make_pca_workspace(H, W, n, q, params: Params, device="cuda") -> Workspace:
+    nb = L.load().nyf_pca_nlm_workspace_size(H, W, n, q, C.byref(params.c()))
+    if nb == 0:
+        raise ValueError("unsupported PCA-NLM configuration")
+    return Workspace(nb, device)
+
+
+def pca_nlm(f, q: int, params: Params, mean=None, basis=None, landmarks=None, out=None,
+            ws: Workspace | None = None):
+    """PCA-NLM: the patch guide (radius params.patch_radius) projected on its q leading
+    principal directions (computed from f unless mean and basis are given), then the
+    joint filter with that guide."""
+    lib = L.load()
+    _check_image(f, "f")
+    H, W, n = f.shape
+    out = torch.empty_like(f) if out is None else out
+    ws = ws or make_pca_workspace(H, W, n, q, params, f.device)
+    if landmarks is not None and landmarks.shape != (params.K, q):
+        raise ValueError("landmarks must be K x q")
+    p = params.c()
+    L.check(lib.nyf_filter_pca_nlm(_ptr(f), H, W, n, q, C.byref(p),
+                                   _ptr(None if mean is None else mean.contiguous()),
+                                   _ptr(None if basis is None else basis.contiguous()),
+                                   _ptr(landmarks), _ptr(out), ws.cptr(), ws.nbytes, _stream()),
+            "nyf_filter_pca_nlm")
+    return out
+
+
 def kmeans(X, K, iters=10, seed=0, init_idx=None, ws: Workspace | None = None):
     """k-means landmarks of the rows of X (N x rho): (centroids, labels, qerr)."""
     lib = L.load()

@@ -38,6 +38,7 @@ class Workload:
     sample_frac: float = 1.0     # fraction of pixels k-means clusters (NLM: 0.01)
     kmeans_iters: int = 10
     seed: int = 0
+    pca_dim: int = 0             # >0: PCA-NLM, the patch guide projected on q principal directions
 
     @property
     def H(self) -> int:
@@ -153,6 +154,16 @@ def colour_nlm(seed=SEED_BASE + 4) -> Workload:
     f = voronoi_colour(512, 768, 200, 20.0, seed, ramp=0.1)
     return Workload("colour_nlm_768x512_K32", f, 255.0, 0.0, 20.0 * math.sqrt(75.0), 32,
                     spatial="box", S=10, patch_radius=2, sample_frac=0.01, seed=seed)
+
+
+def colour_pca_nlm(seed=SEED_BASE + 4) -> Workload:
+    """PCA-NLM at the paper's parameters (Sec. IV): the 768 x 512 colour NLM image (noise 20),
+    7x7x3 patches (rho 147) projected on q = 25 principal directions, 21 x 21 box (S = 10),
+    K = 31 landmarks from k-means on a 1 % subsample, theta = 3 x the noise level of the
+    distance between two patches' PCA coordinates: 3 sigma sqrt(2 q) = 424.3."""
+    f = voronoi_colour(512, 768, 200, 20.0, seed, ramp=0.1)
+    return Workload("colour_pca_nlm_768x512_q25_K31", f, 255.0, 0.0, 3.0 * 20.0 * math.sqrt(50.0),
+                    31, spatial="box", S=10, patch_radius=3, sample_frac=0.01, seed=seed, pca_dim=25)
 
 
 def batched_blf(count=64, seed=SEED_BASE + 5, side_lo=128, side_hi=1024):

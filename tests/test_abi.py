@@ -113,3 +113,30 @@ def test_recursive_gaussian_host_checks(lib):
     assert lib.nyf_filter_blf(bad, None, 8, 2017, 3, 3, C.byref(iir), None, bad, bad, 16, None) == 2
     assert lib.nyf_filter_blf(bad, None, 2016, 2016, 3, 3, C.byref(iir), None, bad, bad, 16,
                               None) == 3
+
+
+def test_pca_nlm_host_checks(lib):
+    assert lib.nyf_patch_pca_workspace_size(3, 3) > 0          # 7x7x3 patches, rho 147
+    assert lib.nyf_patch_pca_workspace_size(3, 4) == 0         # rho 243 > 160
+    assert lib.nyf_patch_pca_workspace_size(3, 0) == 0
+    p = _lib.NyfParams(3.0, 424.0, 31, 10, 0, 1e-7, 0, 1, 10, 3, 0.01, 0)
+    s25 = lib.nyf_pca_nlm_workspace_size(512, 768, 3, 25, C.byref(p))
+    p_blf = _lib.NyfParams(3.0, 424.0, 31, 10, 0, 1e-7, 0, 1, 10, 0, 0.01, 0)
+    blf = lib.nyf_workspace_size(512, 768, 3, 25, C.byref(p_blf))
+    assert s25 >= blf + 4 * 25 * 512 * 768                      # plus the 25-dim guide
+    assert lib.nyf_pca_nlm_workspace_size(512, 768, 3, 33, C.byref(p)) == 0   # q > 32
+    bad = C.c_void_p(256)
+    # q out of range, mean without basis, saved planes (no PCA-NLM backward)
+    assert lib.nyf_filter_pca_nlm(bad, 64, 64, 3, 0, C.byref(p), None, None, None, bad, bad, 16,
+                                  None) == 1
+    assert lib.nyf_filter_pca_nlm(bad, 64, 64, 3, 25, C.byref(p), bad, None, None, bad, bad, 16,
+                                  None) == 1
+    q = _lib.NyfParams(3.0, 424.0, 31, 10, 0, 1e-7, 0, 1, 10, 3, 0.01, 0)
+    q.save_for_backward = 1
+    assert lib.nyf_filter_pca_nlm(bad, 64, 64, 3, 25, C.byref(q), None, None, None, bad, bad, 16,
+                                  None) == 1
+    # a valid call gets as far as the workspace check
+    assert lib.nyf_filter_pca_nlm(bad, 64, 64, 3, 25, C.byref(p), None, None, None, bad, bad, 16,
+                                  None) == 3
+    assert lib.nyf_patch_pca(bad, 64, 64, 3, 3, 26, bad, bad, bad, bad, 16, None) == 3
+    assert lib.nyf_patch_pca(bad, 64, 64, 3, 3, 148, bad, bad, bad, bad, 16, None) == 1
