@@ -326,36 +326,41 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_pca(const float* __re
   }
 }
 
-// ---- the q output columns re-orthonormalised in FP64 (two passes of modified
-// Gram-Schmidt): the FP32 rotations leave them orthonormal only to ~1e-4
+// ---- the q output columns re-orthonormalised in FP64 by classical Gram-Schmidt
+// applied twice (CGS2): the FP32 rotations leave them orthonormal only to
+// ~1e-4.  All dot products of one column are taken at once (a warp per earlier
+// column), so a column costs four barriers.
 __global__ void k_orthonormalize(float* __restrict__ basis, int rho, int q) {
   __shared__ double v[160];
+  __shared__ double d[32];
   __shared__ double red[8];
-  const int tid = threadIdx.x;
-  auto block_sum = [&](double x) {
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if ((tid & 31) == 0) red[tid >> 5] = x;
-    __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    __syncthreads();
-    return s;
-  };
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
   for (int j = 0; j < q; ++j) {
     for (int i = tid; i < rho; i += blockDim.x) v[i] = (double)basis[i * q + j];
     __syncthreads();
-    for (int pass = 0; pass < 2; ++pass)
-      for (int k = 0; k < j; ++k) {
-        double d = 0.0;
-        for (int i = tid; i < rho; i += blockDim.x) d += v[i] * (double)basis[i * q + k];
-        d = block_sum(d);
-        for (int i = tid; i < rho; i += blockDim.x) v[i] -= d * (double)basis[i * q + k];
-        __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int k = warp; k < j; k += nwarp) {          // d_k = u_k . v
+        double s = 0.0;
+        for (int i = lane; i < rho; i += 32) s += v[i] * (double)basis[i * q + k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) d[k] = s;
       }
+      __syncthreads();
+      for (int i = tid; i < rho; i += blockDim.x) {     // v -= sum_k d_k u_k
+        double t = v[i];
+        for (int k = 0; k < j; ++k) t -= d[k] * (double)basis[i * q + k];
+        v[i] = t;
+      }
+      __syncthreads();
+    }
     double nn = 0.0;
     for (int i = tid; i < rho; i += blockDim.x) nn += v[i] * v[i];
-    nn = block_sum(nn);
-    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    if (lane == 0) red[warp] = nn;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < nwarp; ++w) tot += red[w];
+    const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
     for (int i = tid; i < rho; i += blockDim.x) basis[i * q + j] = (float)(v[i] * inv);
     __syncthreads();
   }
