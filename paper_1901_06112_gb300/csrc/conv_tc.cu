@@ -97,7 +97,7 @@ __device__ __forceinline__ void bar_arrive(uint64_t* b) {
 }
 
 // Named barrier among the 128 builder threads (warps 0-3), and the same
-// barrier as an AND vote (every builder gets the same verdict).
+// barrier as an AND vote (every builder gets the same result).
 __device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, 128;\n" ::: "memory"); }
 __device__ __forceinline__ bool builders_all(bool v) {
   uint32_t r;

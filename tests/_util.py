@@ -1,8 +1,8 @@
 """Shared helpers of the parity tests (no method arithmetic here)."""
 import numpy as np
 
-FP32_REL_RMSE = 1e-4      # spec tolerance for the FP32 path
-BF16_REL_RMSE = 2e-3      # spec tolerance for the BF16 path
+FP32_REL_RMSE = 1e-4      # relative RMSE bar of the FP32 path against the FP64 oracle
+BF16_REL_RMSE = 2e-3      # relative RMSE bar of the BF16 path against the FP64 oracle
 
 
 def rel_rmse(got, want):
