@@ -13,9 +13,10 @@
 //                   matrix sum (p - s)(p - s)^T (FP32 within a CTA, one partial
 //                   per CTA);
 //   k_gram_reduce   FP64 sum of the partials, the covariance and the mean;
-//   k_jacobi_pca    one CTA: cyclic Jacobi with round-robin ordering on the
-//                   rho x rho covariance in FP32 (shared memory), eigenvalues
-//                   sorted descending, the q leading eigenvectors;
+//   k_eig_pca       one CTA: Householder tridiagonalisation, bisection for every
+//                   eigenvalue and inverse iteration for the q leading
+//                   eigenvectors, in FP32 (shared memory);
+//   k_orthonormalize the q columns re-orthonormalised in FP64;
 //   k_pca_project   p~(x) for every pixel (16 x 16 tiles, one thread per pixel).
 #include <math.h>
 
@@ -30,8 +31,6 @@ constexpr int kGramCtas = 2 * 152;
 constexpr int kBpt = 4;                 // Gram blocks per thread
 constexpr int kSumCtas = 152;
 constexpr int kJacobiThreads = 512;
-constexpr int kJacobiSweeps = 20;
-constexpr uint32_t kStatusJacobi = NYF_ERR_TIMEOUT;
 
 __device__ inline int reflect101(int i, int n) {
   if (n == 1) return 0;
@@ -181,148 +180,229 @@ __global__ void k_gram_reduce(const float* __restrict__ part, int nparts, int rh
   if (i < rho && threadIdx.x == 0) mean[i] = (float)(msh[i] + (double)shift[i % n]);
 }
 
-// ---- one-CTA Jacobi on the rp x rp covariance (FP32), then sort and basis
-__global__ void __launch_bounds__(kJacobiThreads) k_jacobi_pca(const float* __restrict__ C, int rho, int q,
-                                                               float* __restrict__ eigvals,
-                                                               float* __restrict__ basis,
-                                                               DevState* state) {
+// ---- one-CTA symmetric eigensolver for the rho x rho covariance (FP32):
+//   1. Householder tridiagonalisation T = Q^T C Q (reflector k kept in the
+//      zeroed column k of A; warps over rows, lanes along rows);
+//   2. every eigenvalue of T by bisection on Sturm counts (one thread each;
+//      the count is the number of negative pivots of the LDL^T factorisation
+//      of T - x I);
+//   3. the q leading eigenvectors of T by inverse iteration (4 steps from a
+//      fixed start vector; tridiagonal Gaussian elimination with partial
+//      pivoting on lane 0 of warp 0), each step reorthogonalised against the
+//      earlier vectors whose eigenvalues lie within 1e-3 ||T|| (a cluster);
+//   4. back-transformation u = Q x through the reflectors (a warp per vector).
+// Every loop has a fixed trip count.
+constexpr int kBisectIters = 64;
+constexpr int kInvIters = 4;
+
+__device__ __forceinline__ float block_sum_f(float x, float* red, int tid) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((tid & 31) == 0) red[tid >> 5] = x;
+  __syncthreads();
+  float s = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// Number of eigenvalues of the tridiagonal (d, e2 = e^2) strictly below x.
+__device__ int sturm_count(const float* d, const float* e2, int n, float x, float pivmin) {
+  int c = 0;
+  float q = 1.f;
+  for (int k = 0; k < n; ++k) {
+    q = (d[k] - x) - (k > 0 ? e2[k - 1] / q : 0.f);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f;
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(kJacobiThreads) k_eig_pca(const float* __restrict__ C, int rho, int q,
+                                                            float* __restrict__ eigvals,
+                                                            float* __restrict__ basis, DevState* state) {
   extern __shared__ float smj[];
-  const int rp = (rho + 3) & ~3;                 // even
-  const int ld = rp + 1;
-  float* A = smj;                                // rp x ld
-  float* V = A + rp * ld;                        // rp x ld
-  float* cs = V + rp * ld;                       // rp / 2 cosines
-  float* sn = cs + rp / 2;                       // rp / 2 sines
-  int* top = reinterpret_cast<int*>(sn + rp / 2);
-  int* bot = top + rp / 2;
-  int* order = bot + rp / 2;                     // rp
+  const int n = rho, rp = (rho + 3) & ~3, ld = n | 1;
+  float* A = smj;                                // n x ld
+  float* X = A + n * ld;                         // q columns of n (eigenvectors of T, then of C)
+  float* d = X + n * q;
+  float* e = d + n;
+  float* e2 = e + n;
+  float* beta = e2 + n;
+  float* lam = beta + n;                         // ascending
+  float* vv = lam + n;                           // reflector / work vector
+  float* pw = vv + n;                            // p, then w
+  float* ga = pw + n;                            // elimination: pivots
+  float* gu1 = ga + n;                           //   first superdiagonal
+  float* gu2 = gu1 + n;                          //   second superdiagonal
+  float* gx = gu2 + n;                           //   right-hand side / solution
   __shared__ float red[kJacobiThreads / 32];
-  __shared__ int done;
-  const int tid = threadIdx.x, m = rp / 2;
-  const int warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
-  for (int e = tid; e < rp * rp; e += blockDim.x) {
-    const int i = e / rp, j = e % rp;
-    A[i * ld + j] = C[e];
-    V[i * ld + j] = i == j ? 1.f : 0.f;
-  }
+  __shared__ float bounds[3];                    // lo, hi, ||T||
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
+  (void)state;                                   // fixed trip counts: no status to latch
+  for (int i = warp; i < n; i += nwarp)
+    for (int j = lane; j < n; j += 32) A[i * ld + j] = C[(size_t)i * rp + j];
   __syncthreads();
-  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
-    // off-diagonal and total squared norms
-    float off = 0.f, tot = 0.f;
-    for (int e = tid; e < rp * rp; e += blockDim.x) {
-      const int i = e / rp, j = e % rp;
-      const float a = A[i * ld + j];
-      tot += a * a;
-      if (i != j) off += a * a;
+  // ---- 1. tridiagonalisation
+  for (int k = 0; k < n - 2; ++k) {
+    float ss = 0.f;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) ss += A[i * ld + k] * A[i * ld + k];
+    const float sig = sqrtf(block_sum_f(ss, red, tid));
+    const float x0 = A[(k + 1) * ld + k];
+    if (!(sig > 0.f)) {                          // column already reduced (uniform)
+      if (tid == 0) {
+        e[k] = 0.f;
+        beta[k] = 0.f;
+      }
+      __syncthreads();
+      continue;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if ((tid & 31) == 0) red[tid >> 5] = off;
+    const float alpha = x0 >= 0.f ? -sig : sig;
+    const float b = 1.f / (sig * (sig + fabsf(x0)));
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) vv[i] = i == k + 1 ? x0 - alpha : A[i * ld + k];
     __syncthreads();
+    for (int i = k + 1 + warp; i < n; i += nwarp) {       // p = b B v
+      float t = 0.f;
+      for (int j = k + 1 + lane; j < n; j += 32) t = fmaf(A[i * ld + j], vv[j], t);
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) pw[i] = b * t;
+    }
+    __syncthreads();
+    float vp = 0.f;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) vp += vv[i] * pw[i];
+    const float K = 0.5f * b * block_sum_f(vp, red, tid);
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) pw[i] -= K * vv[i];   // w
+    __syncthreads();
+    for (int i = k + 1 + warp; i < n; i += nwarp)            // B -= v w^T + w v^T
+      for (int j = k + 1 + lane; j < n; j += 32)
+        A[i * ld + j] -= vv[i] * pw[j] + pw[i] * vv[j];
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) A[i * ld + k] = vv[i];   // keep the reflector
     if (tid == 0) {
-      float so = 0.f;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) so += red[w];
-      red[0] = so;
+      e[k] = alpha;
+      beta[k] = b;
     }
     __syncthreads();
-    const float offs = red[0];
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = tot;
-    __syncthreads();
-    if (tid == 0) {
-      float st = 0.f;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) st += red[w];
-      done = offs <= 1e-13f * st;
-      if (sweep == kJacobiSweeps - 1 && !done) atomicCAS(&state->status, 0, (int)kStatusJacobi);
-    }
-    __syncthreads();
-    if (done) break;
-    for (int step = 0; step < rp - 1; ++step) {
-      // circle-method pairing in closed form: index rp - 1 meets `step`, and
-      // (step + k, step - k) mod (rp - 1) for k = 1 .. m - 1
-      for (int k = tid; k < m; k += blockDim.x) {
-        const int a0 = k == 0 ? step : (step + k) % (rp - 1);
-        const int b0 = k == 0 ? rp - 1 : (step - k + rp - 1) % (rp - 1);
-        const int p = min(a0, b0), qq = max(a0, b0);
-        top[k] = p;
-        bot[k] = qq;
-        const float apq = A[p * ld + qq];
-        float c = 1.f, s = 0.f;
-        if (fabsf(apq) > 1e-30f) {
-          const float tau = (A[qq * ld + qq] - A[p * ld + p]) / (2.f * apq);
-          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-          c = rsqrtf(1.f + t * t);
-          s = t * c;
-        }
-        cs[k] = c;
-        sn[k] = s;
-      }
-      __syncthreads();
-      for (int k = warp; k < m; k += nwarp) {               // rows p, q of A
-        const int p = top[k], qq = bot[k];
-        const float c = cs[k], s = sn[k];
-        for (int j = lane; j < rp; j += 32) {
-          const float a = A[p * ld + j], b = A[qq * ld + j];
-          A[p * ld + j] = c * a - s * b;
-          A[qq * ld + j] = s * a + c * b;
-        }
-      }
-      __syncthreads();
-      for (int k = warp; k < m; k += nwarp) {               // columns p, q of A and V
-        const int p = top[k], qq = bot[k];
-        const float c = cs[k], s = sn[k];
-        for (int i = lane; i < rp; i += 32) {
-          const float a = A[i * ld + p], b = A[i * ld + qq];
-          A[i * ld + p] = c * a - s * b;
-          A[i * ld + qq] = s * a + c * b;
-          const float va = V[i * ld + p], vb = V[i * ld + qq];
-          V[i * ld + p] = c * va - s * vb;
-          V[i * ld + qq] = s * va + c * vb;
-        }
-      }
-      __syncthreads();
-    }
   }
-  // eigenvalues as Rayleigh quotients v_i^T C v_i / v_i^T v_i on the unrotated
-  // covariance: the diagonal the rotations leave, and the norms of the
-  // accumulated FP32 columns, carry their rounding (~1e-5 of lambda_max at
-  // rho = 147); C V (FP32, into A's storage) and the quotients (FP64 sums) are
-  // accurate to ~1e-6.
-  for (int a = warp; a < rp; a += nwarp)
-    for (int i = lane; i < rp; i += 32) {
-      float s = 0.f;
-      for (int b = 0; b < rp; ++b) s = fmaf(C[(size_t)a * rp + b], V[b * ld + i], s);
-      A[a * ld + i] = s;
-    }
-  __syncthreads();
-  float* lam = cs;                               // rp floats (cs and sn are contiguous)
-  for (int i = tid; i < rp; i += blockDim.x) {   // v^T C v / v^T v: the FP32 columns drift off unit norm
-    double l = 0.0, nn = 0.0;
-    for (int a = 0; a < rp; ++a) {
-      const double va = (double)V[a * ld + i];
-      l += va * (double)A[a * ld + i];
-      nn += va * va;
-    }
-    lam[i] = (float)(nn > 0.0 ? l / nn : 0.0);
+  if (tid == 0) {
+    if (n >= 2) e[n - 2] = A[(n - 1) * ld + (n - 2)];
+    e[n - 1] = 0.f;
   }
   __syncthreads();
-  // rank of each real eigenvalue (descending, ties by index); padding ranks last
-  for (int i = tid; i < rp; i += blockDim.x) {
-    int rank = 0;
-    const float li = i < rho ? lam[i] : -INFINITY;
-    for (int j = 0; j < rp; ++j) {
-      const float lj = j < rho ? lam[j] : -INFINITY;
-      rank += (lj > li) || (lj == li && j < i);
-    }
-    order[rank] = i;
+  for (int i = tid; i < n; i += blockDim.x) {
+    d[i] = A[i * ld + i];
+    e2[i] = e[i] * e[i];
   }
   __syncthreads();
-  for (int k = tid; k < rho; k += blockDim.x) eigvals[k] = lam[order[k]];
-  for (int e = tid; e < rho * q; e += blockDim.x) {
-    const int i = e / q, j = e % q;
-    basis[e] = V[i * ld + order[j]];
+  if (tid == 0) {                                // Gershgorin interval and ||T||
+    float lo = INFINITY, hi = -INFINITY;
+    for (int i = 0; i < n; ++i) {
+      const float rad = fabsf(e[i]) + (i > 0 ? fabsf(e[i - 1]) : 0.f);
+      lo = fminf(lo, d[i] - rad);
+      hi = fmaxf(hi, d[i] + rad);
+    }
+    bounds[0] = lo;
+    bounds[1] = hi;
+    bounds[2] = fmaxf(fabsf(lo), fabsf(hi));
+  }
+  __syncthreads();
+  const float tnorm = bounds[2];
+  const float eps = 1.1920929e-7f;
+  const float pivmin = fmaxf(1e-30f, 1e-2f * eps * eps * tnorm * tnorm);
+  // ---- 2. bisection: thread i finds the i-th smallest eigenvalue
+  for (int i = tid; i < n; i += blockDim.x) {
+    float a = bounds[0], b = bounds[1];
+    for (int it = 0; it < kBisectIters; ++it) {
+      const float mid = 0.5f * (a + b);
+      if (!(mid > a && mid < b)) break;
+      if (sturm_count(d, e2, n, mid, pivmin) <= i) a = mid;
+      else b = mid;
+      if (b - a <= 2.f * eps * fmaxf(fabsf(a), fabsf(b)) + pivmin) break;
+    }
+    lam[i] = 0.5f * (a + b);
+  }
+  __syncthreads();
+  // ---- 3. inverse iteration for the q largest, warp 0 (lane 0 solves)
+  if (warp == 0) {
+    const float tiny = eps * tnorm, ortol = 1e-3f * tnorm;
+    for (int j = 0; j < q; ++j) {
+      const float lj = lam[n - 1 - j];
+      for (int i = lane; i < n; i += 32) gx[i] = (float)((37 * (i + 1) + 11 * j) % 97) / 97.f - 0.5f;
+      __syncwarp();
+      for (int it = 0; it < kInvIters; ++it) {
+        if (lane == 0) {                         // (T - lj I) y = gx, partial pivoting
+          for (int k = 0; k < n; ++k) {
+            ga[k] = d[k] - lj;
+            gu1[k] = k < n - 1 ? e[k] : 0.f;
+            gu2[k] = 0.f;
+          }
+          for (int k = 0; k < n - 1; ++k) {
+            const float sub = e[k];
+            if (fabsf(ga[k]) >= fabsf(sub)) {
+              if (ga[k] == 0.f) ga[k] = tiny;
+              const float m = sub / ga[k];
+              ga[k + 1] -= m * gu1[k];
+              gx[k + 1] -= m * gx[k];
+            } else {
+              const float m = ga[k] / sub;
+              const float uk = gu1[k];
+              const float u1n = ga[k + 1];
+              const float u2n = k + 1 < n - 1 ? gu1[k + 1] : 0.f;
+              ga[k] = sub;
+              ga[k + 1] = uk - m * u1n;
+              gu1[k] = u1n;
+              gu2[k] = u2n;
+              if (k + 1 < n - 1) gu1[k + 1] = -m * u2n;
+              const float xk = gx[k];
+              gx[k] = gx[k + 1];
+              gx[k + 1] = xk - m * gx[k + 1];
+            }
+          }
+          for (int k = n - 1; k >= 0; --k) {
+            float s = gx[k];
+            if (k + 1 < n) s -= gu1[k] * gx[k + 1];
+            if (k + 2 < n) s -= gu2[k] * gx[k + 2];
+            gx[k] = s / (ga[k] != 0.f ? ga[k] : tiny);
+          }
+        }
+        __syncwarp();
+        for (int i2 = 0; i2 < j; ++i2) {         // reorthogonalise inside the cluster
+          if (!(fabsf(lam[n - 1 - i2] - lj) < ortol)) continue;
+          const float* xi = X + i2 * n;
+          float dt = 0.f;
+          for (int i = lane; i < n; i += 32) dt += xi[i] * gx[i];
+          for (int o = 16; o > 0; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
+          for (int i = lane; i < n; i += 32) gx[i] -= dt * xi[i];
+          __syncwarp();
+        }
+        float nn = 0.f;
+        for (int i = lane; i < n; i += 32) nn += gx[i] * gx[i];
+        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        const float inv = nn > 0.f ? rsqrtf(nn) : 0.f;
+        for (int i = lane; i < n; i += 32) gx[i] *= inv;
+        __syncwarp();
+      }
+      for (int i = lane; i < n; i += 32) X[j * n + i] = gx[i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // ---- 4. u_j = H_0 H_1 ... H_{n-3} x_j, a warp per vector
+  for (int j = warp; j < q; j += nwarp) {
+    float* x = X + j * n;
+    for (int k = n - 3; k >= 0; --k) {
+      const float bk = beta[k];
+      if (bk == 0.f) continue;
+      float dt = 0.f;
+      for (int i = k + 1 + lane; i < n; i += 32) dt += A[i * ld + k] * x[i];
+      for (int o = 16; o > 0; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
+      for (int i = k + 1 + lane; i < n; i += 32) x[i] -= bk * dt * A[i * ld + k];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < rho; k += blockDim.x) eigvals[k] = lam[n - 1 - k];
+  for (int e3 = tid; e3 < rho * q; e3 += blockDim.x) {
+    const int i = e3 / q, j = e3 % q;
+    basis[e3] = X[j * n + i];
   }
 }
 
@@ -446,8 +526,8 @@ size_t pca_scratch_bytes(int n, int r) {
 }
 
 size_t pca_jacobi_smem(int rho) {
-  const int rp = (rho + 3) & ~3;
-  return sizeof(float) * (2 * (size_t)rp * (rp + 1) + rp) + sizeof(int) * (size_t)(rp + rp);
+  const int ld = rho | 1;
+  return sizeof(float) * ((size_t)rho * ld + (size_t)rho * 32 + 11 * (size_t)rho);
 }
 
 cudaError_t launch_patch_pca(const float* f, int H, int W, int n, int r, int q, void* scratch,
@@ -475,9 +555,9 @@ cudaError_t launch_patch_pca(const float* f, int H, int W, int n, int r, int q, 
   k_patch_gram<<<kGramCtas, kGramThreads, gsm, st>>>(f, H, W, n, r, rho, shift, part);
   k_gram_reduce<<<rp, 128, 0, st>>>(part, kGramCtas, rho, N, shift, n, C, mean);
   const size_t jsm = pca_jacobi_smem(rho);
-  e = cudaFuncSetAttribute(k_jacobi_pca, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
+  e = cudaFuncSetAttribute(k_eig_pca, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
   if (e != cudaSuccess) return e;
-  k_jacobi_pca<<<1, kJacobiThreads, jsm, st>>>(C, rho, q, eigvals, basis, state);
+  k_eig_pca<<<1, kJacobiThreads, jsm, st>>>(C, rho, q, eigvals, basis, state);
   k_orthonormalize<<<1, 256, 0, st>>>(basis, rho, q);
   count_launches(6);
   return cudaGetLastError();
