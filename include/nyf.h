@@ -194,6 +194,17 @@ nyf_status nyf_filter_nlm(const float* f, int H, int W, int n, const nyf_params*
                           const float* landmarks, float* out, void* ws, size_t ws_bytes,
                           void* stream);
 
+/* Diagnostic for NYF_GAUSSIAN_IIR (host only, no GPU work): the parameters one
+ * line direction of length len uses, as computed on the host in FP64 and rounded
+ * to FP32.  out[0..3] = B, -B, g1, -e2 of the difference form
+ *   dl = B x[i] - B w[i-2] + g1 d1 - e2 d2,  w[i] = w[i-1] + dl
+ * (d1 = w[i-1] - w[i-2], d2 = w[i-2] - w[i-3]); out[4] = LS, values per lane of
+ * the line padded with zeros to 32 LS; out[5] = len; out[6 + 9 d .. ] = the 3 x 3
+ * matrix T^(LS 2^d), d = 0..4 (row-major, basis (w, d1, d2), T the step with zero
+ * input); out[51..59] = Rm, the anticausal state entering at the padded end from
+ * the causal state at its last value.  out_len >= 60. */
+nyf_status nyf_iir_line_params(double sigma_s, int len, float* out, int out_len);
+
 /* ---- PCA-NLM (Sec. IV: the paper's NLM experiments use principal-neighbourhood
  * NLM).  The patch guide p(x) of nyf_filter_nlm (rho = n (2r+1)^2 <= 160, r =
  * params->patch_radius >= 1) is replaced by its coordinates in the q leading

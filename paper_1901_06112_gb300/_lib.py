@@ -74,6 +74,7 @@ _SIGNATURES.update({
                                                   _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "nyf_batched_stats": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(NyfParams), C.c_int,
                                     C.POINTER(NyfStats), _P]),
+    "nyf_iir_line_params": (C.c_int, [C.c_double, C.c_int, C.POINTER(C.c_float), C.c_int]),
     "nyf_patch_pca_workspace_size": (C.c_size_t, [C.c_int, C.c_int]),
     "nyf_patch_pca": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P,
                                 C.c_size_t, _P]),

@@ -130,6 +130,28 @@ Line make_line(double sigma, int len) {
 
 }  // namespace
 
+}  // namespace nyf
+
+// Diagnostic: the host-computed parameters of one line direction (no GPU work).
+extern "C" nyf_status nyf_iir_line_params(double sigma_s, int len, float* out, int out_len) {
+  using namespace nyf;
+  if (!out || out_len < 60 || !(sigma_s >= 0.5) || !(sigma_s <= 1e4) || len < 1) return NYF_ERR_INVALID_ARG;
+  if (lane_values(len) < 0) return NYF_ERR_UNSUPPORTED;
+  const Line L = make_line(sigma_s, len);
+  out[0] = L.B;
+  out[1] = L.nB;
+  out[2] = L.g1;
+  out[3] = L.ne2;
+  out[4] = (float)L.LS;
+  out[5] = (float)L.len;
+  for (int d = 0; d < 5; ++d)
+    for (int i = 0; i < 9; ++i) out[6 + 9 * d + i] = L.P[d][i];
+  for (int i = 0; i < 9; ++i) out[51 + i] = L.Rm[i];
+  return NYF_OK;
+}
+
+namespace nyf {
+
 bool iir_supported(int H, int W, int n) {
   (void)n;
   return lane_values(H) > 0 && lane_values(W) > 0;
