@@ -62,7 +62,10 @@ CPU_SAMPLE = (192, 192)     # crop of the workload the oracle filters (and diffe
 # on the 1920 x 1080, K = 32 workload, from the ncu captures summarised in
 # profiles/ncu_conv_kernels_colour_blf_1920x1080.md; only for the kernels as captured.
 NCU_TRAFFIC = {("conv_bwd", "fp32"): 1.420e9 + 0.253e9, ("conv_bwd", "bf16"): 1.420e9 + 0.253e9,
-               ("conv_combine", "fp32"): 0.323e9 + 1.035e9, ("conv_combine", "bf16"): 0.315e9 + 1.034e9}
+               ("conv_combine", "fp32"): 0.323e9 + 1.035e9, ("conv_combine", "bf16"): 0.315e9 + 1.034e9,
+               # both recursive-Gaussian passes (k_cols + k_rows), sigma_s 5, from
+               # profiles/ncu_recursive_gaussian_colour_blf_1920x1080.md
+               ("recursive_pair", "fp32"): 0.625e9 + 1.025e9 + 1.327e9 + 0.032e9}
 
 
 def hbm_peak():
@@ -321,7 +324,9 @@ def iir_extra(nyf, lib, f_dev, wl, steps, flush, stream):
             "status": st["status"], "conv_ms": stages[3],
             "roofline": {"kernel": "k_cols + k_rows (both passes)", "bound": "hbm",
                          "achieved": a, "peak": pk, "unit": "GB/s", "frac": a / pk,
-                         "traffic": None, "algorithmic_GB": gb,
+                         "traffic": NCU_TRAFFIC[("recursive_pair", "fp32")]
+                         if (H, W, planes) == (1080, 1920, 32) else None,
+                         "algorithmic_GB": gb,
                          "peak_basis": f"copy bandwidth ({how})"}}
 
 
@@ -467,7 +472,8 @@ def main():
         a_h = gb / (stage_mean[3] / 1e3)
         roof_fwd = {"kernel": "k_cols + k_rows (both recursive passes)", "bound": "hbm",
                     "achieved": a_h, "peak": pk_h, "unit": "GB/s", "frac": a_h / pk_h,
-                    "traffic": None, "launch_ms": stage_mean[3], "algorithmic_GB": gb,
+                    "traffic": NCU_TRAFFIC[("recursive_pair", "fp32")] if captured else None,
+                    "launch_ms": stage_mean[3], "algorithmic_GB": gb,
                     "peak_basis": f"copy bandwidth ({how_h})"}
     roof_bwd = roof("conv_bwd", bwd_flops, stage_mean[4]) if fwdbwd else None
     dominant = roof_bwd if (fwdbwd and stage_mean[4] > stage_mean[3]) else roof_fwd
