@@ -141,8 +141,6 @@ bool ws_ok(const void* ws, size_t have, size_t need) {
   return ws && (reinterpret_cast<uintptr_t>(ws) & 255) == 0 && have >= need;
 }
 
-nyf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? NYF_OK : NYF_ERR_CUDA; }
-
 #define NYF_TRY(expr)                                   \
   do {                                                  \
     cudaError_t _e = (expr);                            \
