@@ -135,3 +135,34 @@ def test_full_size_1920x1080_k32(nyf):
     want = iir.nystrom_filter_iir(w.f, w.f, mu.astype(np.float64), w.sigma_r, w.sigma_s, 1e-7)
     r, _ = report("iir blf 1920x1080 K=32 (all pixels)", out, want)
     assert r < FP32_REL_RMSE
+
+
+def test_pca_nlm_with_the_recursive_gaussian(nyf):
+    # PCA guide (Sec. IV PCA-NLM) with the recursive Gaussian as omega
+    from oracle import pca
+    w = synth.colour_pca_nlm()
+    f = w.f[:64, :80].copy()
+    g, m, U = pca.pca_guide(f.astype(np.float64), 2, 10)
+    mf, Uf = m.astype(np.float32), U.astype(np.float32)
+    g, _, _ = pca.pca_guide(f.astype(np.float64), 2, 10, mf.astype(np.float64), Uf.astype(np.float64))
+    mu = _landmarks(g.reshape(-1, 10), 8)
+    want = _oracle(f, g, mu, w.sigma_r, 2.0)
+    P = nyf.Params(sigma_s=2.0, sigma_r=w.sigma_r, K=8, spatial="gaussian_iir", patch_radius=2)
+    out = nyf.pca_nlm(cuda(f), 10, P, mean=cuda(mf), basis=cuda(Uf), landmarks=cuda(mu))
+    r, _ = report("pca-nlm 64x80 q=10 with the recursive Gaussian", out.cpu().numpy(), want)
+    assert r < FP32_REL_RMSE
+
+
+def test_batched_recursive_gaussian_equals_single_image_calls(nyf):
+    # uneven images with their own sigma_s, sigma_r through the batched entry point
+    shapes = [(40, 56), (33, 20), (64, 64)]
+    ss, sr = [1.5, 3.0, 5.0], [30.0, 45.0, 25.0]
+    imgs = [synth.voronoi_colour(h, w_, 12, 8.0, h * 100 + w_) for h, w_ in shapes]
+    P = nyf.Params(K=6, kmeans_iters=5, spatial="gaussian_iir")
+    bt = nyf.Batched(shapes, ss, sr, P, backward=False)
+    got = bt.unpack(bt.forward(bt.pack(imgs)))
+    for b, im in enumerate(imgs):
+        Pb = nyf.Params(sigma_s=ss[b], sigma_r=sr[b], K=6, kmeans_iters=5, spatial="gaussian_iir")
+        one = nyf.blf(cuda(im), Pb).cpu().numpy()
+        r, _ = report(f"batched recursive image {b} vs single call", got[b].cpu().numpy(), one)
+        assert r < 1e-6
