@@ -68,6 +68,22 @@ NCU_TRAFFIC = {("conv_bwd", "fp32"): 1.420e9 + 0.253e9, ("conv_bwd", "bf16"): 1.
                ("recursive_pair", "fp32"): 0.625e9 + 1.025e9 + 1.327e9 + 0.032e9}
 
 
+def weak_scaling_value(ms, megapixels, world, device, dist=None):
+    """Max over ranks of the per-step time and the whole-job throughput: every rank
+    filters its own replica (one image each), so value = ranks x megapixels / slowest."""
+    import torch
+    t = torch.tensor([float(ms)], device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * megapixels / (ms_max / 1e3)
+
+
+def replica_seed(base_seed, rank):
+    """Seed of rank `rank`'s replica (each rank draws its own landmarks)."""
+    return base_seed + rank
+
+
 def hbm_peak():
     """Measured copy bandwidth (GB/s) on this machine type, else the fallback."""
     try:
@@ -396,7 +412,8 @@ def main():
 
     def make(precision, bwd=False):
         return nyf.Params(sigma_s=wl.sigma_s, sigma_r=wl.sigma_r, K=wl.K,
-                          kmeans_iters=wl.kmeans_iters, seed=wl.seed + rank, precision=precision,
+                          kmeans_iters=wl.kmeans_iters, seed=replica_seed(wl.seed, rank),
+                          precision=precision,
                           save_for_backward=bwd, spatial=args.spatial)
 
     P = make(args.precision, fwdbwd)
@@ -437,12 +454,8 @@ def main():
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     mp = H * W / 1e6
-    value = world * mp / (ms_max / 1e3)
+    ms_max, value = weak_scaling_value(ms, mp, world, dev, dist)
 
     r = st["rank"]
     planes = wl.K if r > 0 else 0
