@@ -275,6 +275,13 @@ nyf_status nyf_filter_blf_backward(const float* f, const float* guide, int H, in
  * Returns NYF_ERR_INVALID_ARG for other sizes. */
 nyf_status nyf_selftest_umma(float* D, int N, int K, int a_in_tmem, int* status, void* stream);
 
+/* Self-test of the bounded device waits every waiting kernel uses (the paper
+ * has no counterpart): one warp waits for an mbarrier phase that nothing
+ * completes, gives up after `limit` polls (1..4096, each at most ~1 us) and
+ * latches NYF_ERR_TIMEOUT into *status (device int, zeroed first).  Nothing
+ * traps or hangs; the context stays usable. */
+nyf_status nyf_selftest_wait_timeout(int limit, int* status, void* stream);
+
 /* ---- Batched filtering of images of uneven sizes (one workload, one call).
  * Image b of the batch is the H_b x W_b x n HWC block starting at element
  * items[b].offset of the packed buffers f / out / grad_out / grad_f (device);

@@ -64,6 +64,7 @@ _SIGNATURES = {
     "nyf_features_static": (C.c_int, [_P, C.c_int64, C.c_int, _P, C.c_int, C.c_float, C.c_double,
                                       C.c_int, _P, _P, _P, _P]),
     "nyf_selftest_umma": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "nyf_selftest_wait_timeout": (C.c_int, [C.c_int, _P, _P]),
 }
 OPTIONAL = {}
 _SIGNATURES.update({

@@ -94,10 +94,33 @@ __global__ void __launch_bounds__(128, 1) k_umma_selftest(float* __restrict__ D,
   if (warp == 0) umma::tmem_dealloc(tbase, ncols);
 }
 
+// Bounded-wait self-test: an mbarrier that nothing ever arrives on, waited for
+// with `limit` polls (each at most ~1 us).  The wait gives up, the kernel
+// latches NYF_ERR_TIMEOUT into *status and returns; nothing traps or hangs.
+__global__ void k_wait_timeout_selftest(uint32_t limit, int* __restrict__ status) {
+  __shared__ uint64_t mbar;
+  if (threadIdx.x == 0) {
+    umma::mbar_init(&mbar, 1);
+    umma::fence_mbar_init();
+  }
+  __syncthreads();
+  const bool ok = __all_sync(0xffffffffu, umma::mbar_wait(&mbar, 0, limit));
+  if (!ok && threadIdx.x == 0) atomicCAS(status, 0, (int)NYF_ERR_TIMEOUT);
+}
+
 }  // namespace
 }  // namespace nyf
 
 using namespace nyf;
+
+extern "C" nyf_status nyf_selftest_wait_timeout(int limit, int* status, void* stream) {
+  if (!status || limit < 1 || limit > 4096) return NYF_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return NYF_ERR_CUDA;
+  k_wait_timeout_selftest<<<1, 32, 0, st>>>((uint32_t)limit, status);
+  count_launches(1);
+  return cudaGetLastError() == cudaSuccess ? NYF_OK : NYF_ERR_CUDA;
+}
 
 extern "C" nyf_status nyf_selftest_umma(float* D, int N, int K, int a_in_tmem, int* status,
                                         void* stream) {

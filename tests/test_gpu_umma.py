@@ -47,3 +47,27 @@ def test_tcgen05_gemm(lib, N, K, a_in_tmem):
     err = np.abs(got - want).max()
     print(f"[parity] tcgen05 128x{N}x{K} (A in {'TMEM' if a_in_tmem else 'smem'}): max abs err {err:.2e}")
     assert err <= 1e-5 * max(1.0, np.abs(want).max())
+
+
+@pytest.mark.parametrize("limit", [1, 64])
+def test_bounded_wait_gives_up_and_reports_timeout(lib, limit):
+    # an mbarrier phase nothing completes: the wait must give up after `limit`
+    # polls and latch NYF_ERR_TIMEOUT (6); the context stays usable afterwards
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.nyf_selftest_wait_timeout(limit, C.c_void_p(status.data_ptr()), stream) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 6
+    D = torch.zeros((128, 64), dtype=torch.float32, device="cuda")
+    assert lib.nyf_selftest_umma(C.c_void_p(D.data_ptr()), 64, 32, 0, C.c_void_p(status.data_ptr()),
+                                 stream) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    A, B = operands(64, 32)
+    assert np.abs(D.cpu().numpy() - A @ B.T).max() <= 1e-5 * np.abs(A @ B.T).max()
+
+
+def test_bounded_wait_rejects_bad_limits(lib):
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert lib.nyf_selftest_wait_timeout(0, C.c_void_p(status.data_ptr()), None) == 1
+    assert lib.nyf_selftest_wait_timeout(5000, C.c_void_p(status.data_ptr()), None) == 1
