@@ -154,13 +154,19 @@ nyf_status nyf_features(const float* guide, int64_t N, int rho, const float* lan
  * without a device allocator, a plugin whose host owns all device memory, a
  * latency-critical loop where cudaMalloc would synchronise the device).  The
  * paper has no counterpart: this is a deployment variant of nyf_features.
- * Same arguments and results as nyf_features, without ws/ws_bytes: its scratch
- * (status word, W_hat factor, FP64 eigendecomposition buffers) is a fixed
- * 256 KiB array in device memory that every GPU loading the library holds
- * until the process exits.  The first call on a device looks up that array's
- * address (cudaGetSymbolAddress, with the device current) and caches it; make
- * that first call before any stream capture.  All calls share the array and it
- * keeps the last call's contents, so calls that overlap on the GPU race.
+ * Same arguments, argument checks and results as nyf_features, without
+ * ws/ws_bytes: its scratch (status word, W_hat factor, FP64 eigendecomposition
+ * buffers) is a fixed 256 KiB array in device memory that every GPU loading the
+ * library holds until the process exits.  The first call on a device looks up
+ * that array's address (cudaGetSymbolAddress, with the device current) and
+ * caches it; make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents, so calls that overlap on the
+ * GPU race.
+ *   status  1 int output (device), or NULL: written, stream-ordered after the
+ *           call's work, with the status the device latched -- NYF_OK, or
+ *           NYF_ERR_NUMERIC when no eigenvalue was kept (rank 0), in which case
+ *           phi was NOT written.  The latched word lives in the library's own
+ *           array, so this output is the only way to see a device-side error.
  * Returns NYF_ERR_UNSUPPORTED for K > NYF_STATIC_MAX_K or
  * rho > NYF_STATIC_MAX_RHO, NYF_ERR_CUDA if the address lookup fails.
  * Allocates nothing. */
@@ -168,7 +174,7 @@ nyf_status nyf_features(const float* guide, int64_t N, int rho, const float* lan
 #define NYF_STATIC_MAX_RHO 160
 nyf_status nyf_features_static(const float* guide, int64_t N, int rho, const float* landmarks,
                                int K, float sigma_r, double eig_rel_tol, int precision, void* phi,
-                               int* rank, double* alphas, void* stream);
+                               int* rank, double* alphas, int* status, void* stream);
 
 /* Nystrom bilateral filter, Algorithm 1 with output Eqs. (14)-(15).
  *   f          H x W x n image (device)
@@ -217,9 +223,11 @@ nyf_status nyf_iir_line_params(double sigma_s, int len, float* out, int out_len)
 
 /* Mean patch, all rho eigenvalues of C (descending) and the q leading
  * eigenvectors.  Covariance accumulated in FP32 per CTA from patches shifted by
- * the channel means, reduced in FP64; eigendecomposition by cyclic Jacobi in
- * FP32 on one CTA (NYF_ERR_TIMEOUT latched in ws if it has not converged after
- * 20 sweeps).
+ * the channel means, reduced in FP64; eigendecomposition in FP32 on one CTA:
+ * Householder tridiagonalisation, every eigenvalue by bisection on Sturm
+ * counts, the q leading eigenvectors by inverse iteration (reorthogonalised
+ * within clusters of close eigenvalues) and back-transformation, then the q
+ * columns re-orthonormalised in FP64.  Every loop has a fixed trip count.
  *   mean     rho floats (device, out)
  *   basis    rho x q floats, row-major: basis[i * q + j] = component i of
  *            eigenvector j (device, out)
@@ -290,8 +298,11 @@ nyf_status nyf_selftest_wait_timeout(int limit, int* status, void* stream);
  * fields of *params; landmarks come from k-means per image.  The images are
  * spread over a small pool of internal streams of the current device, forked
  * from and joined back to `stream` with events, so the whole call can be
- * captured into a CUDA graph and replayed.  Do not issue batched calls on the
- * same device from several host threads at once (they share the pool). */
+ * captured into a CUDA graph and replayed.  The pool (streams and events) is
+ * created by the first batched call made on a device, so make that first call
+ * outside any stream capture (stream creation is not allowed while a capture
+ * is in progress).  Do not issue batched calls on the same device from several
+ * host threads at once (they share the pool). */
 typedef struct {
   int64_t offset;   /* first element of image b in the packed buffers */
   int H, W;
@@ -304,10 +315,13 @@ typedef struct {
 size_t nyf_batched_workspace_size(const nyf_batch_item* items, int B, int n,
                                   const nyf_params* params);
 
-/* Forward of every image (as nyf_filter_blf with guide = image). */
+/* Forward of every image (as nyf_filter_blf with guide = image).
+ *   landmarks  B x K x n floats (device; image b's K x n landmarks start at
+ *              landmarks + b K n), or NULL: k-means per image
+ *              (params->kmeans_iters, params->seed) as nyf_filter_blf does. */
 nyf_status nyf_filter_blf_batched(const float* f, const nyf_batch_item* items, int B, int n,
-                                  const nyf_params* params, float* out, void* ws, size_t ws_bytes,
-                                  void* stream);
+                                  const nyf_params* params, const float* landmarks, float* out,
+                                  void* ws, size_t ws_bytes, void* stream);
 
 /* Backward of every image (as nyf_filter_blf_backward), after the batched
  * forward on the same workspace.  grad_sigma: 2 B floats (device),

@@ -62,7 +62,7 @@ _SIGNATURES = {
     "nyf_get_timing": (C.c_int, [C.POINTER(C.c_float), C.c_int]),
     "nyf_launch_count": (C.c_longlong, []),
     "nyf_features_static": (C.c_int, [_P, C.c_int64, C.c_int, _P, C.c_int, C.c_float, C.c_double,
-                                      C.c_int, _P, _P, _P, _P]),
+                                      C.c_int, _P, _P, _P, _P, _P]),
     "nyf_selftest_umma": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
     "nyf_selftest_wait_timeout": (C.c_int, [C.c_int, _P, _P]),
 }
@@ -70,7 +70,7 @@ OPTIONAL = {}
 _SIGNATURES.update({
     "nyf_batched_workspace_size": (C.c_size_t, [_P, C.c_int, C.c_int, C.POINTER(NyfParams)]),
     "nyf_filter_blf_batched": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(NyfParams), _P, _P,
-                                         C.c_size_t, _P]),
+                                         _P, C.c_size_t, _P]),
     "nyf_filter_blf_batched_backward": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(NyfParams),
                                                   _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "nyf_batched_stats": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(NyfParams), C.c_int,

@@ -470,7 +470,7 @@ nyf_status check_pca(int H, int W, int n, int r, int q) {
 
 extern "C" {
 
-int nyf_version(void) { return 100; }
+int nyf_version(void) { return 101; }
 
 void nyf_set_timing(int enable) {
   std::lock_guard<std::mutex> lk(g_timing_mu);
@@ -722,13 +722,15 @@ nyf_status nyf_filter_pca_nlm(const float* f, int H, int W, int n, int q, const 
 }
 
 nyf_status nyf_filter_blf_batched(const float* f, const nyf_batch_item* items, int B, int n,
-                                  const nyf_params* p, float* out, void* ws, size_t ws_bytes,
-                                  void* stream) {
-  if (!f || !out) return NYF_ERR_INVALID_ARG;
+                                  const nyf_params* p, const float* landmarks, float* out, void* ws,
+                                  size_t ws_bytes, void* stream) {
+  if (!f || !out || !p || (landmarks && !aligned4(landmarks))) return NYF_ERR_INVALID_ARG;
+  const int64_t lm_stride = (int64_t)p->K * n;
   return run_batched(items, B, n, p, ws, ws_bytes, stream,
                      [&](int b, const nyf_params& q, void* wsb, size_t wsn, cudaStream_t s) {
                        const nyf_batch_item& it = items[b];
-                       return blf_impl(f + it.offset, nullptr, it.H, it.W, n, n, &q, nullptr,
+                       return blf_impl(f + it.offset, nullptr, it.H, it.W, n, n, &q,
+                                       landmarks ? landmarks + b * lm_stride : nullptr,
                                        out + it.offset, wsb, wsn, s, false);
                      });
 }

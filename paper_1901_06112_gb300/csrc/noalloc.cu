@@ -15,7 +15,9 @@
 // call should come before any stream capture.  All calls share the array and
 // it keeps the last call's contents: the status word is cleared on every call,
 // and calls that overlap on the GPU (different streams, or different host
-// threads on the same device) race on it.
+// threads on the same device) race on it.  Because the status word lives in
+// the library's array, where no caller can read it, each call copies it, once
+// its work is done, to the caller's nullable `status` output.
 #include <mutex>
 
 #include "nyf_internal.cuh"
@@ -58,9 +60,11 @@ using namespace nyf;
 extern "C" nyf_status nyf_features_static(const float* guide, int64_t N, int rho,
                                           const float* landmarks, int K, float sigma_r,
                                           double eig_rel_tol, int precision, void* phi, int* rank,
-                                          double* alphas, void* stream) {
+                                          double* alphas, int* status, void* stream) {
+  // the same argument rules as nyf_features
   if (!guide || !landmarks || !phi || N < 1 || N > ((int64_t)1 << 31) || rho < 1 ||
-      !(sigma_r > 0.f) || !(eig_rel_tol >= 0.0) || (precision != NYF_FP32 && precision != NYF_BF16))
+      !(sigma_r > 0.f) || !isfinite(sigma_r) || !(eig_rel_tol >= 0.0) ||
+      (precision != NYF_FP32 && precision != NYF_BF16))
     return NYF_ERR_INVALID_ARG;
   // sizes beyond what the fixed scratch (and the kernels' shared memory) hold
   if (K < 1 || K > NYF_STATIC_MAX_K || rho > NYF_STATIC_MAX_RHO) return NYF_ERR_UNSUPPORTED;
@@ -79,6 +83,11 @@ extern "C" nyf_status nyf_features_static(const float* guide, int64_t N, int rho
     return NYF_ERR_CUDA;
   if (launch_features(guide, N, rho, landmarks, K, sigma_r, what, state, phi,
                       precision == NYF_BF16, st) != cudaSuccess)
+    return NYF_ERR_CUDA;
+  // the latched device status (NYF_ERR_NUMERIC when no mode was kept and phi was
+  // not written) into the caller's own device int
+  if (status &&
+      cudaMemcpyAsync(status, &state->status, sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return NYF_ERR_CUDA;
   return NYF_OK;
 }

@@ -378,11 +378,17 @@ class Batched:
             out.append(flat[o:o + H * W * self.n].view(H, W, self.n))
         return out
 
-    def forward(self, f, out=None):
+    def forward(self, f, out=None, landmarks=None):
+        """Forward of every image; landmarks: None (k-means per image) or a
+        B x K x n float32 CUDA tensor."""
         out = torch.empty_like(f) if out is None else out
+        if landmarks is not None and not (
+                landmarks.is_cuda and landmarks.dtype == torch.float32
+                and landmarks.is_contiguous() and landmarks.shape == (self.B, self.params.K, self.n)):
+            raise ValueError("landmarks must be a contiguous float32 CUDA tensor of B x K x n")
         L.check(self.lib.nyf_filter_blf_batched(_ptr(f), self.items, self.B, self.n,
-                                                C.byref(self._p), _ptr(out), self.ws.cptr(),
-                                                self.ws.nbytes, _stream()),
+                                                C.byref(self._p), _ptr(landmarks), _ptr(out),
+                                                self.ws.cptr(), self.ws.nbytes, _stream()),
                 "nyf_filter_blf_batched")
         return out
 
@@ -401,21 +407,23 @@ class Batched:
                 "nyf_batched_stats")
         return {k: getattr(s, k) for k, _ in L.NyfStats._fields_}
 
-    def capture(self, f, grad_out):
-        """Record forward + backward on static buffers into a CUDA graph."""
-        self.f_static, self.g_static = f, grad_out
+    def capture(self, f, grad_out, landmarks=None):
+        """Record forward + backward on static buffers into a CUDA graph (the
+        warm-up call before it also creates the library's stream pool outside
+        the capture)."""
+        self.f_static, self.g_static, self.lm_static = f, grad_out, landmarks
         self.out_static = torch.empty_like(f)
         self.gf_static = torch.empty_like(f)
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):                # warm-up outside the graph
-            self.forward(f, self.out_static)
+            self.forward(f, self.out_static, landmarks)
             self.backward(f, self.out_static, grad_out, self.gf_static)
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
-            self.forward(self.f_static, self.out_static)
+            self.forward(self.f_static, self.out_static, self.lm_static)
             self.backward(self.f_static, self.out_static, self.g_static, self.gf_static)
         return self.out_static, self.gf_static, self.grad_sigma
 

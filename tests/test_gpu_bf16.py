@@ -1,5 +1,7 @@
-"""Parity of the BF16 path (features stored in bfloat16, convolutions on the
-tensor cores for S <= 16) with the FP64 oracle: relative RMSE <= 2e-3."""
+"""Parity of the BF16 path (features kept in float32, convolutions on the
+tensor cores for S <= 16 with phi f and the vertical-pass result rounded to
+bfloat16, FP32 accumulation) with the FP64 oracle: relative RMSE <= 2e-3.
+nyf_features with precision bf16 stores the features themselves in bfloat16."""
 import math
 
 import numpy as np

@@ -85,7 +85,7 @@ def test_colour_1920x1080_device_kmeans(nyf, hd):
 def test_hyperspectral_512x512x31_sampled_parity(nyf):
     w = synth.hyperspectral_blf()
     X = w.f.reshape(-1, 31).astype(np.float64)
-    mu, info = pl.landmarks(X, w.K, 5, w.seed)
+    mu, info = pl.landmarks(X, w.K, w.kmeans_iters, w.seed)
     mu = mu.astype(np.float32)
     P = _params(nyf, w)
     ws = nyf.make_workspace(w.H, w.W, 31, 31, P)
