@@ -259,6 +259,84 @@ def conv_bwd_flops_per_pixel(K, n, S):
 
 STAGES = ["landmarks", "eig", "features", "conv_combine", "bwd_conv", "bwd_features"]
 
+# Peaks of the step roofline.  FP32: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (derived
+# from the unit counts and the maximum clock).  SFU: 16 special-function results per SM
+# and clock (the exp of the features) x 152 SMs x 2070 MHz, derived the same way.
+SFU_PER_SM_CLK = 16
+
+
+def peaks():
+    """Roofline denominators: HBM GB/s and BF16 TFLOP/s sustained (measured), FP32 TFLOP/s
+    and SFU Gop/s (derived)."""
+    hbm, how = hbm_peak()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            tc, tc_how = float(json.load(fh)["bf16_tflops_sustained"]), "measured"
+    except (OSError, ValueError, KeyError):
+        tc, tc_how = 1700.0, "fallback"
+    fp32 = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    sfu = SMS * SFU_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e9
+    return {"hbm_GBs": hbm, "tc_TFLOPs": tc, "fp32_TFLOPs": fp32, "sfu_Gops": sfu,
+            "basis": f"HBM copy ({how}), BF16 dense sustained ({tc_how}); FP32 and SFU derived "
+                     "from 152 SMs x 128 lanes x 2 FLOP and x 16 results per clock at 2070 MHz"}
+
+
+def stage_counts(N, n, rho, K, T, iters, Ns, fwdbwd, conv_tensor=False, feat_tensor=None,
+                 keep_planes=True, nlm_r=0):
+    """Algorithmic work of each stage of one step (the method's own counts, not the
+    kernels'): {stage: (bytes, fp32 FLOP, tensor FLOP, exp)}.
+
+    N pixels, n channels, rho guide dimension, K modes, T = 2S + 1 taps, `iters` Lloyd
+    iterations on Ns rows.  k-means: 3 rho K FLOP per row and iteration, the rows read
+    once per iteration.  Features: the distance contraction 2 rho K, exp, E W_hat 2 K^2
+    per pixel (on the tensor cores for rho >= 16); guide (or, for NLM, image) read, phi
+    written.  Convolutions: per plane 2 passes x T taps x 2 FLOP + 2 for the combine
+    (forward), 5 passes + 10 (backward, over the saved planes C); f and phi read, g_hat
+    and eta written, C written (forward) and read (backward) when kept.
+    """
+    if feat_tensor is None:
+        feat_tensor = rho >= 16
+    q = n + 1
+    c = {}
+    c["landmarks"] = (4.0 * rho * Ns * iters, 3.0 * rho * K * Ns * iters, 0.0, 0.0)
+    c["eig"] = (0.0, 0.0, 0.0, 0.0)         # K x K, latency only
+    guide_bytes = 4 * n if nlm_r else 4 * rho
+    feat_flop = (2.0 * rho * K + 2.0 * K * K) * N
+    c["features"] = (N * (guide_bytes + 4.0 * K), 0.0 if feat_tensor else feat_flop,
+                     feat_flop if feat_tensor else 0.0, float(N * K))
+    conv_flop = N * K * q * (2.0 * T * 2 + 2)
+    cbytes = 4.0 * K * q * N if (fwdbwd and keep_planes) else 0.0
+    c["conv_combine"] = (N * (4.0 * n + 4.0 * K + 4.0 * n + 4.0) + cbytes,
+                         0.0 if conv_tensor else conv_flop, conv_flop if conv_tensor else 0.0, 0.0)
+    if fwdbwd:
+        bflop = N * K * q * (5.0 * T * 2 + 10)
+        if not keep_planes:
+            bflop += conv_flop
+        c["bwd_conv"] = (N * (4.0 * K + 8.0 * q + 4.0 * n * 3 + 4.0 + 4.0 * K + 4.0 * n) + cbytes,
+                         bflop, 0.0, 0.0)
+        c["bwd_features"] = (N * (4.0 * K + 4.0 * rho + 8.0 * n),
+                             N * (4.0 * K * K + 4.0 * rho * K), 0.0, float(N * K))
+    return c
+
+
+def step_roofline(counts, stage_ms, step_ms):
+    """Sec. 8(d) roofline time of a step: sum over stages of the largest of bytes / HBM,
+    FP32 FLOP / FP32 peak, tensor FLOP / tensor peak and exp / SFU rate; frac = that
+    sum / the measured step time.  Also the binding resource of each stage."""
+    pk = peaks()
+    total, per = 0.0, {}
+    for s, (b, fl, tc, ex) in counts.items():
+        times = {"hbm": b / (pk["hbm_GBs"] * 1e9), "fp32": fl / (pk["fp32_TFLOPs"] * 1e12),
+                 "tensor": tc / (pk["tc_TFLOPs"] * 1e12), "sfu": ex / (pk["sfu_Gops"] * 1e9)}
+        bound = max(times, key=times.get)
+        t = times[bound] * 1e3
+        total += t
+        got = stage_ms.get(s)
+        per[s] = {"bound": bound, "roofline_ms": t, "measured_ms": got,
+                  "frac": (t / got) if got else None}
+    return {"roofline_ms": total, "step_ms": step_ms, "frac": total / step_ms, "stages": per,
+            "peaks": pk}
+
 
 def timed_steps(step, steps, flush, stream, lib):
     """Per-step CUDA-event times (ms) and per-stage library event times."""
@@ -281,6 +359,111 @@ def timed_steps(step, steps, flush, stream, lib):
     means = [float(np.mean(st[:, i][st[:, i] >= 0])) if np.any(st[:, i] >= 0) else None
              for i in range(7)]
     return float(np.mean(step_ms)), means
+
+
+def golden_landmarks(name):
+    """The oracle's k-means landmarks of a workload, stored by tests/golden/make_landmarks.py."""
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import make_landmarks
+    return make_landmarks.load(name)
+
+
+def _rel(got, want):
+    got, want = np.asarray(got, np.float64), np.asarray(want, np.float64)
+    return float(np.linalg.norm(got - want) / np.linalg.norm(want)), float(np.max(np.abs(got - want)))
+
+
+def accuracy_blf(nyf, w, mu, precision, fwdbwd, samples=256, guide=None):
+    """The library's output on workload w with the oracle's landmarks mu against the FP64
+    oracle (Algorithm 1 by direct window sums) on `samples` seeded pixels; with fwdbwd also
+    the gradients w.r.t. the image and both sigmas for a cotangent on a 24 x 24 window,
+    against the oracle's autograd on the window grown by S (exact there)."""
+    import torch
+    from oracle import grad as gr
+    from oracle import kernels as Kr
+    from oracle import nystrom as ny
+    from paper_1901_06112_gb300 import synth
+    sr = float(np.float32(w.sigma_r))
+    P = nyf.Params(sigma_s=w.sigma_s, sigma_r=sr, K=w.K, precision=precision, spatial=w.spatial,
+                   S=w.S, patch_radius=w.patch_radius, sample_frac=w.sample_frac)
+    f = torch.from_numpy(w.f).cuda()
+    mut = torch.from_numpy(np.ascontiguousarray(mu, np.float32)).cuda()
+    taps = Kr.box_taps(w.radius) if w.spatial == "box" else Kr.gaussian_taps(w.sigma_s, w.radius)
+    idx = synth.sample_indices(w.H * w.W, samples, 17)
+    ys, xs = idx // w.W, idx % w.W
+    if w.patch_radius > 0:
+        from oracle import guide as gd
+        out = nyf.nlm(f, P, landmarks=mut).cpu().numpy()
+        p = gd.patch_guide(w.f.astype(np.float64), w.patch_radius)
+    else:
+        out = nyf.blf(f, P, landmarks=mut).cpu().numpy()
+        p = w.f
+    want = ny.nystrom_filter_at(w.f, p, mu.astype(np.float64), sr, taps, 1e-7, ys, xs)
+    r, m = _rel(out[ys, xs], want)
+    acc = {"vs": f"FP64 oracle, Algorithm 1 with the oracle's k-means landmarks, {len(ys)} pixels",
+           "rel_rmse": r, "max_abs": m}
+    if fwdbwd and w.patch_radius == 0:
+        S, h = w.radius, 24
+        y0, x0 = w.H // 2 - h // 2, w.W // 2 - h // 2
+        G = np.zeros(w.f.shape, np.float32)
+        G[y0:y0 + h, x0:x0 + h] = np.random.default_rng(7).normal(size=(h, h, w.n))
+        res = nyf.blf_vjp(f, P, torch.from_numpy(G).cuda(), landmarks=mut)
+        c0, c1 = (max(0, y0 - S), min(w.H, y0 + h + S)), (max(0, x0 - S), min(w.W, x0 + h + S))
+        crop = w.f[c0[0]:c0[1], c1[0]:c1[1]]
+        ref = gr.vjp(crop, crop, mu, sr, w.sigma_s, S, 1e-7, G[c0[0]:c0[1], c1[0]:c1[1]],
+                     guide_is_image=True)
+        rg, mg = _rel(res["df"].cpu().numpy()[c0[0]:c0[1], c1[0]:c1[1]], ref["df"])
+        acc["grad_f"] = {"rel_rmse": rg, "max_abs": mg, "window": f"{h}x{h} at ({y0},{x0})"}
+        for nm in ("dsigma_r", "dsigma_s"):
+            acc[nm] = {"rel": abs(res[nm] - ref[nm]) / abs(ref[nm])}
+    return acc
+
+
+def config_line(nyf, lib, w, golden, precision, fwdbwd, steps, flush, stream):
+    """One workload measured like the headline: the whole call (k-means on the device,
+    eig, features, convolutions [, backward]) per step, per-stage CUDA events, the
+    Sec. 8(d) step roofline, and the accuracy pass with the oracle's landmarks."""
+    import torch
+    H, W, n = w.f.shape
+    sr = float(np.float32(w.sigma_r))
+    P = nyf.Params(sigma_s=w.sigma_s, sigma_r=sr, K=w.K, kmeans_iters=w.kmeans_iters, seed=w.seed,
+                   precision=precision, spatial=w.spatial, S=w.S, patch_radius=w.patch_radius,
+                   sample_frac=w.sample_frac, save_for_backward=fwdbwd)
+    f = torch.from_numpy(w.f).cuda()
+    rho = n * (2 * w.patch_radius + 1) ** 2 if w.patch_radius else n
+    ws = nyf.make_workspace(H, W, n, rho, P)
+    out = torch.empty_like(f)
+    G = torch.randn(f.shape, generator=torch.Generator().manual_seed(1)).cuda()
+    grads = nyf.BackwardBuffers(f)
+
+    def step():
+        if w.patch_radius:
+            nyf.nlm(f, P, out=out, ws=ws)
+        else:
+            nyf.blf(f, P, out=out, ws=ws)
+        if fwdbwd:
+            nyf.blf_backward(f, P, out, G, ws, grads)
+    lib.nyf_set_timing(1)
+    for _ in range(3):
+        step()
+    ms, stages = timed_steps(step, steps, flush, stream, lib)
+    lib.nyf_set_timing(0)
+    st = nyf.stats(ws)
+    N = H * W
+    Ns = max(1, int(np.floor(w.sample_frac * N + 0.5)))
+    planes = w.K if st["rank"] > 0 else 0
+    counts = stage_counts(N, n, rho, planes, 2 * w.radius + 1, w.kmeans_iters, Ns, fwdbwd,
+                          conv_tensor=precision == "bf16" and w.radius <= 16 and n <= 3,
+                          nlm_r=w.patch_radius)
+    sm = {k: v for k, v in zip(STAGES, stages[:6]) if v is not None}
+    line = {"workload": w.name, "mode": "fwd+bwd" if fwdbwd else "fwd", "precision": precision,
+            "value": N / 1e6 / (ms / 1e3), "unit": "megapixels/s", "ms_per_step": ms,
+            "stages_ms": sm, "status": st["status"], "rank_r": st["rank"],
+            "roofline_step": step_roofline(counts, sm, ms)}
+    blocks, errs = golden_landmarks(golden)
+    line["kmeans_qerr_rel"] = abs(st["qerr"] - errs[0]) / errs[0]
+    line["accuracy"] = accuracy_blf(nyf, w, blocks[0], precision, fwdbwd)
+    return line
 
 
 def batched_extra(nyf, steps, warmup, flush, stream, precision="bf16"):
@@ -309,9 +492,42 @@ def batched_extra(nyf, steps, warmup, flush, stream, precision="bf16"):
         ms.append(e0.elapsed_time(e1))
     mpix = bt.total / 3 / 1e6
     t = float(np.mean(ms))
-    return {"workload": f"batched_blf_64_images_128-1024_K16_{precision}", "images": len(batch),
+    # Sec. 8(d) step roofline: the stages' algorithmic work summed over the images
+    tot = {}
+    for w in batch:
+        c = stage_counts(w.H * w.W, 3, 3, 16, 2 * w.radius + 1, 10, w.H * w.W, True,
+                         conv_tensor=precision == "bf16" and w.radius <= 16)
+        for k, v in c.items():
+            tot[k] = tuple(a + b for a, b in zip(tot.get(k, (0.0,) * 4), v))
+    roof = step_roofline(tot, {}, t)
+    line = {"workload": f"batched_blf_64_images_128-1024_K16_{precision}", "images": len(batch),
             "megapixels": mpix, "ms_per_step": t, "value": mpix / (t / 1e3),
-            "unit": "megapixels/s", "mode": "fwd+bwd, one CUDA-graph replay per step"}
+            "unit": "megapixels/s", "mode": "fwd+bwd, one CUDA-graph replay per step",
+            "roofline_step": roof}
+    # accuracy: the same batched call with the oracle's landmarks, checked images against
+    # the FP64 oracle on sampled pixels
+    try:
+        from oracle import kernels as Kr
+        from oracle import nystrom as ny
+        blocks, _ = golden_landmarks("batched")
+        lm = torch.from_numpy(np.stack(blocks).astype(np.float32)).cuda()
+        outs = bt.unpack(bt.forward(f, landmarks=lm))
+        worst, worst_max = 0.0, 0.0
+        for b in (0, 7, 23, 41, 63):
+            w = batch[b]
+            idx = synth.sample_indices(w.H * w.W, 64, b)
+            ys, xs = idx // w.W, idx % w.W
+            want = ny.nystrom_filter_at(w.f, w.f, blocks[b].astype(np.float64),
+                                        float(np.float32(w.sigma_r)),
+                                        Kr.gaussian_taps(w.sigma_s, w.radius), 1e-7, ys, xs)
+            r, m = _rel(outs[b].cpu().numpy()[ys, xs], want)
+            worst, worst_max = max(worst, r), max(worst_max, m)
+        line["accuracy"] = {"vs": "FP64 oracle with the oracle's landmarks, images 0, 7, 23, 41, "
+                                  "63, 64 pixels each (worst image)",
+                            "rel_rmse": worst, "max_abs": worst_max}
+    except Exception as ex:      # the accuracy pass must not hide the measurement
+        line["accuracy"] = {"error": str(ex)[:200]}
+    return line
 
 
 def iir_extra(nyf, lib, f_dev, wl, steps, flush, stream):
@@ -490,6 +706,19 @@ def main():
                     "peak_basis": f"copy bandwidth ({how_h})"}
     roof_bwd = roof("conv_bwd", bwd_flops, stage_mean[4]) if fwdbwd else None
     dominant = roof_bwd if (fwdbwd and stage_mean[4] > stage_mean[3]) else roof_fwd
+    # Sec. 8(d) step roofline of the headline step
+    counts = stage_counts(H * W, n, n, planes, 2 * P.radius + 1, wl.kmeans_iters, H * W, fwdbwd,
+                          conv_tensor=args.precision == "bf16" and P.radius <= 16)
+    step_roof = step_roofline(counts, {k: v for k, v in zip(STAGES, stage_mean[:6])
+                                       if v is not None}, ms)
+    accuracy = None
+    if rank == 0 and not iir:
+        try:
+            blocks, errs = golden_landmarks("colour_hd")
+            accuracy = accuracy_blf(nyf, wl, blocks[0], args.precision, fwdbwd)
+            accuracy["kmeans_qerr_rel"] = abs(st["qerr"] - errs[0]) / errs[0]
+        except Exception as ex:           # the accuracy pass must not hide the measurement
+            accuracy = {"error": str(ex)[:300]}
 
     extras = {}
     if not args.no_extras and rank == 0:
@@ -526,6 +755,18 @@ def main():
                 extras["pca_nlm"] = pca_nlm_extra(nyf, max(3, args.steps // 4), flush, stream)
             except Exception as ex:
                 extras["pca_nlm"] = {"error": str(ex)[:300]}
+        # the other single-GPU workloads, each measured like the headline
+        configs = {}
+        for key, make_w, golden, bwd in (("colour_256", synth.colour_blf_small, "colour_256", True),
+                                         ("hyperspectral", synth.hyperspectral_blf, "hyperspectral",
+                                          True),
+                                         ("nlm", synth.colour_nlm, "nlm", False)):
+            try:
+                configs[key] = config_line(nyf, lib, make_w(), golden, "fp32", bwd,
+                                           max(3, args.steps // 2), flush, stream)
+            except Exception as ex:
+                configs[key] = {"error": str(ex)[:300]}
+        extras["configs"] = configs
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -567,7 +808,9 @@ def main():
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{world}"},
             "stages_ms": dict(zip(STAGES, stage_mean[:6])),
+            "accuracy": accuracy,
             "roofline": dominant,
+            "roofline_step": step_roof,
             "roofline_conv_fwd": roof_fwd,
             "e2e": e2e,
             "gpu_launches": int(launches),

@@ -91,12 +91,21 @@ typedef struct {
   int patch_radius;   /* NLM: guide = (2r+1)^2 x n patch, reflect-101 border */
   float sample_frac;  /* fraction of pixels k-means clusters, (0, 1] */
   int conv_tile;      /* nyf_tile: convolution kernel variant */
-  int save_for_backward; /* nonzero: nyf_filter_blf also keeps, in the workspace, the
-                            K (n+1) convolved planes C_kq = omega * (phi_k f_q) that
-                            nyf_filter_blf_backward reads (the workspace grows by
-                            K (n+1) H W floats plus the backward scratch; see
-                            nyf_workspace_size).  Zero: forward-only workspace. */
+  int save_for_backward; /* nyf_save: what nyf_filter_blf keeps in the workspace for
+                            nyf_filter_blf_backward.  NYF_SAVE_NONE: forward-only
+                            workspace.  NYF_SAVE_PLANES: the K (n+1) convolved planes
+                            C_kq = omega * (phi_k f_q) (the workspace grows by
+                            K (n+1) H W floats plus the backward scratch).
+                            NYF_SAVE_RECOMPUTE: the features and eta only; the backward
+                            convolves C_kq again, NYF_RECOMPUTE_MODES modes at a time,
+                            so the planes take min(K, NYF_RECOMPUTE_MODES) (n+1) H W
+                            floats (the backward costs about the forward's
+                            convolutions more).  Other values: NYF_ERR_INVALID_ARG. */
 } nyf_params;
+
+/* nyf_params.save_for_backward */
+typedef enum { NYF_SAVE_NONE = 0, NYF_SAVE_PLANES = 1, NYF_SAVE_RECOMPUTE = 2 } nyf_save;
+#define NYF_RECOMPUTE_MODES 4
 
 /* Device-side results of the last call on a workspace (nyf_get_stats). */
 typedef struct {
@@ -258,7 +267,9 @@ nyf_status nyf_filter_pca_nlm(const float* f, int H, int W, int n, int q, const 
 /* Adjoint of nyf_filter_blf (the paper has no gradients; derived from
  * Eqs. (9)-(15)).  Must follow the nyf_filter_blf call that produced `out`
  * on the same workspace, with the same f, guide and params, and
- * params->save_for_backward nonzero (else NYF_ERR_INVALID_ARG).  Landmarks are
+ * params->save_for_backward NYF_SAVE_PLANES or NYF_SAVE_RECOMPUTE (else
+ * NYF_ERR_INVALID_ARG).  With NYF_SAVE_RECOMPUTE the convolved planes are
+ * formed again, in FP32, a few modes at a time.  Landmarks are
  * held fixed; the window radius S is held at its forward value; the kept
  * modes are held fixed.  Given grad_out = dL/d g_hat (H x W x n):
  *   grad_f      H x W x n output dL/df; if guide was NULL this is the total

@@ -18,6 +18,8 @@ STATUS_NAMES = {0: "NYF_OK", 1: "NYF_ERR_INVALID_ARG", 2: "NYF_ERR_UNSUPPORTED",
 FP32, BF16 = 0, 1
 GAUSSIAN, BOX, GAUSSIAN_IIR = 0, 1, 2
 TILE_AUTO, TILE_WIDE, TILE_NARROW, TILE_TENSOR = 0, 1, 2, 3
+SAVE_NONE, SAVE_PLANES, SAVE_RECOMPUTE = 0, 1, 2
+RECOMPUTE_MODES = 4
 MAX_K, MAX_RHO, MAX_S, MAX_CHANNELS = 64, 160, 32, 64
 
 

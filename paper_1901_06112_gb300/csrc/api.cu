@@ -49,7 +49,8 @@ WsLayout ws_layout(const WsShape& s) {
   L.spart = take(s.bwd ? sizeof(float) * backward_spart_floats(s.H, s.W, s.n) : 0);
   L.gw = take(s.bwd ? sizeof(double) * (2 * K * K + K) : 0);
   L.adj = take(s.bwd ? sizeof(float) * nq1 * N : 0);
-  L.cbuf = take(s.bwd ? sizeof(float) * K * nq1 * N : 0);
+  const size_t kc = s.recompute ? std::min(K, (size_t)kRecomputeModes) : K;
+  L.cbuf = take(s.bwd ? sizeof(float) * kc * nq1 * N : 0);
   L.ybuf = take(s.iir ? sizeof(float) * K * nq1 * N : 0);
   L.total = o;
   return L;
@@ -130,6 +131,8 @@ nyf_status check_params(const nyf_params* p, int n) {
   if (n < 1 || n > NYF_MAX_CHANNELS) return NYF_ERR_INVALID_ARG;
   if (p->patch_radius < 0) return NYF_ERR_INVALID_ARG;
   if (p->conv_tile < NYF_TILE_AUTO || p->conv_tile > NYF_TILE_TENSOR) return NYF_ERR_INVALID_ARG;
+  if (p->save_for_backward < NYF_SAVE_NONE || p->save_for_backward > NYF_SAVE_RECOMPUTE)
+    return NYF_ERR_INVALID_ARG;
   if (p->spatial == NYF_GAUSSIAN_IIR) return NYF_OK;   // no window radius
   const int S = window_radius(p);
   if (S < 1) return NYF_ERR_INVALID_ARG;
@@ -175,7 +178,8 @@ WsShape shape_for(int H, int W, int n, int rho, const nyf_params* p) {
   s.Ns = subsample_rows(s.N, p->sample_frac);
   s.bf16 = false;   // the filters keep phi in float32 (see nyf_params.precision)
   s.gather = p->patch_radius > 0;
-  s.bwd = p->save_for_backward != 0 && p->patch_radius == 0;
+  s.bwd = p->save_for_backward != NYF_SAVE_NONE && p->patch_radius == 0;
+  s.recompute = p->save_for_backward == NYF_SAVE_RECOMPUTE;
   s.iir = p->spatial == NYF_GAUSSIAN_IIR;
   return s;
 }
@@ -272,7 +276,8 @@ nyf_status blf_impl(const float* f, const float* guide, int H, int W, int n, int
   {
     Stage t(st, 3, timed);
     NYF_TRY(spatial_combine(f, H, W, n, p, tile, w, L, out,
-                            p->save_for_backward ? reinterpret_cast<float*>(w + L.cbuf) : nullptr, st));
+                            p->save_for_backward == NYF_SAVE_PLANES
+                                ? reinterpret_cast<float*>(w + L.cbuf) : nullptr, st));
   }
   return NYF_OK;
 }
@@ -304,10 +309,19 @@ nyf_status blf_backward_impl(const float* f, const float* guide, int H, int W, i
   if (timed) timing_begin(4, 6);
   {
     Stage t(st, 4, timed);
-    NYF_TRY(launch_bwd_conv(f, H, W, n, p->K, p->spatial, p->sigma_s, S, w + L.phi, false,
-                            reinterpret_cast<const float*>(w + L.eta), out, grad_out,
-                            reinterpret_cast<const float*>(w + L.cbuf),
-                            reinterpret_cast<float*>(w + L.adj), grad_f, dphi, spart, state, st));
+    float* cbuf = reinterpret_cast<float*>(w + L.cbuf);
+    // NYF_SAVE_PLANES: one pass over the saved planes.  NYF_SAVE_RECOMPUTE: chunks of
+    // kRecomputeModes modes, each convolved again (C_kq) and then taken through the adjoint.
+    const int chunk = p->save_for_backward == NYF_SAVE_RECOMPUTE ? kRecomputeModes : p->K;
+    for (int k0 = 0; k0 < p->K; k0 += chunk) {
+      if (p->save_for_backward == NYF_SAVE_RECOMPUTE)
+        NYF_TRY(launch_conv_recompute(f, H, W, n, w + L.phi, false, p->spatial, p->sigma_s, S, k0,
+                                      k0 + chunk, state, cbuf, st));
+      NYF_TRY(launch_bwd_conv(f, H, W, n, p->K, p->spatial, p->sigma_s, S, w + L.phi, false,
+                              reinterpret_cast<const float*>(w + L.eta), out, grad_out, cbuf,
+                              reinterpret_cast<float*>(w + L.adj), grad_f, dphi, spart, state, st,
+                              k0, k0 + chunk));
+    }
   }
   {
     Stage t(st, 5, timed);
@@ -470,7 +484,7 @@ nyf_status check_pca(int H, int W, int n, int r, int q) {
 
 extern "C" {
 
-int nyf_version(void) { return 101; }
+int nyf_version(void) { return 102; }
 
 void nyf_set_timing(int enable) {
   std::lock_guard<std::mutex> lk(g_timing_mu);

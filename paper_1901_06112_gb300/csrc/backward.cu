@@ -343,17 +343,21 @@ const double* eig_A64(const void* scratch);
 cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spatial, float sigma_s,
                             int S, const void* phi, bool bf16, const float* eta, const float* out,
                             const float* grad_out, const float* cbuf, float* adj, float* grad_f,
-                            float* dphi, float* spart, const DevState* state, cudaStream_t st) {
+                            float* dphi, float* spart, const DevState* state, cudaStream_t st,
+                            int k_begin, int k_end) {
   const int Sc = conv_compiled_radius(S);
   if (Sc < 0) return cudaErrorInvalidValue;
   const int64_t N = (int64_t)H * W;
-  int64_t g = (N + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
-  k_adjoint<<<(int)g, 256, 0, st>>>(grad_out, out, eta, N, n, adj);
-  count_launches(1);
+  const bool first = k_begin == 0;    // the first chunk of modes forms the adjoint planes
+  if (first) {
+    int64_t g = (N + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    k_adjoint<<<(int)g, 256, 0, st>>>(grad_out, out, eta, N, n, adj);
+    count_launches(1);
+  }
   const int chunks = bwd_chunks(Sc, n);
   cudaError_t e;
-  if (chunks > 1) {
+  if (chunks > 1 && first) {
     e = cudaMemsetAsync(dphi, 0, sizeof(float) * (size_t)K * N, st);
     if (e != cudaSuccess) return e;
   }
@@ -387,6 +391,9 @@ cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spat
     }
     a.taps[kMaxTapRadius + z] = t;
   }
+  a.k_begin = k_begin;
+  a.k_end = k_end;
+  a.accumulate = first ? 0 : 1;
   a.dphi = dphi;
   a.atomic_dphi = chunks > 1 ? 1 : 0;
   a.df = grad_f;

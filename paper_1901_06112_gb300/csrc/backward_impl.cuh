@@ -37,7 +37,9 @@ struct BwdArgs {
   int bf16;
   const DevState* state;
   const float* adj;       // (n + 1) planes of N: a_q
-  const float* cbuf;      // K (n + 1) planes of N: C_kq (plane k (n + 1) + q), saved by the forward
+  const float* cbuf;      // planes C_kq, saved or recomputed: plane (k - k_begin) (n + 1) + q
+  int k_begin, k_end;     // modes processed by this launch (k_end capped at the kept planes)
+  int accumulate;         // add into df and sig_part (a later chunk of modes) instead of writing
   float inv2s2;           // 1 / (2 sigma_s^2)
   float inv_s3;           // 1 / sigma_s^3
   int S_true;
@@ -111,7 +113,8 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_consta
   const int q0 = blockIdx.z * NQ;
   const int n = a.n;
   const int nq = min(NQ, n + 1 - q0);                          // quantities of this CTA
-  const int r = a.state->planes;
+  const int kb = a.k_begin;
+  const int r = min(a.k_end, a.state->planes);                 // modes kb <= k < r
 
   // adjoint planes a_q on the tile + halo (zero outside the image), then phi_0
   for (int e = tid; e < NQ * HH * HW; e += kBwdThreads) {
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_consta
     cp_async4(Aq + qi * PLANE + yy * PS + xx,
               in ? a.adj + (int64_t)(q0 + qi) * a.N + (int64_t)gy * a.W + gx : a.adj, in);
   }
-  if (r > 0) bwd_stage_phi<S>(a, P, 0, ty0, tx0);
+  if (kb < r) bwd_stage_phi<S>(a, P, kb, ty0, tx0);
   cp_async_commit();
 
   // (g, g') tap pairs from the launch parameters: one packed FMA updates the g
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_consta
     for (int j = 0; j < RH; ++j) dfa[qi][j] = 0.f;
   float sig = 0.f;
 
-  for (int k = 0; k < r; ++k) {
+  for (int k = kb; k < r; ++k) {
     cp_async_wait<0>();
     __syncthreads();                 // phi_k (and the adjoint planes) landed; M is free
     float pc[RH];                    // phi_k at this thread's pixels
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_consta
       if (qi < nq) {                 // uniform over the block
         const int q = q0 + qi;
         // C_kq at this thread's pixels, saved by the forward pass
-        const float* Cp = a.cbuf + ((int64_t)k * (n + 1) + q) * a.N + (int64_t)y * a.W + tx0 + hx0;
+        const float* Cp = a.cbuf + ((int64_t)(k - kb) * (n + 1) + q) * a.N + (int64_t)y * a.W + tx0 + hx0;
         float cq[RH];
         if (RH % 4 == 0 && yin && tx0 + hx0 + RH <= a.W &&
             (reinterpret_cast<uintptr_t>(Cp) & 15) == 0) {
@@ -261,7 +264,10 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_consta
         const int64_t pix = (int64_t)y * a.W + x;
 #pragma unroll
         for (int qi = 0; qi < NQ; ++qi)
-          if (q0 + qi < n) a.df[pix * n + q0 + qi] = dfa[qi][j];
+          if (q0 + qi < n) {
+            float* d = a.df + pix * n + q0 + qi;
+            *d = a.accumulate ? *d + dfa[qi][j] : dfa[qi][j];
+          }
       }
     }
   }
@@ -275,7 +281,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_consta
     float s = 0.f;
     for (int w = 0; w < kBwdThreads / 32; ++w) s += red[w];
     const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    a.sig_part[cta] = s;
+    a.sig_part[cta] = a.accumulate ? a.sig_part[cta] + s : s;
   }
 }
 

@@ -76,6 +76,9 @@ cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void*
   a.zeta = split ? zeta_ws : nullptr;
   a.eta = eta_out;
   a.cout = cout;
+  a.k_begin = 0;
+  a.k_end = NYF_MAX_K;
+  a.c_only = 0;
   cudaError_t e;
   if (mma) e = conv_tc_dispatch(a, st);
   else if (Sc <= 8) e = conv_dispatch_a(Sc, a, st);
@@ -87,6 +90,44 @@ cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void*
   k_divide<<<(int)g, 256, 0, st>>>(zeta_ws, eta_out, a.N, n, a.eta_thr, out, state);
   count_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_conv_recompute(const float* f, int H, int W, int n, const void* phi, bool bf16,
+                                  int spatial, float sigma_s, int S, int k_begin, int k_end,
+                                  DevState* state, float* cout, cudaStream_t st) {
+  const int Sc = conv_compiled_radius(S);
+  if (Sc < 0) return cudaErrorInvalidValue;
+  ConvArgs a;
+  a.f = f;
+  a.H = H;
+  a.W = W;
+  a.n = n;
+  a.N = (int64_t)H * W;
+  a.phi = phi;
+  a.bf16 = bf16 ? 1 : 0;
+  a.state = state;
+  a.state_rw = state;
+  a.box = spatial == NYF_BOX ? 1 : 0;
+  a.inv2s2 = a.box ? 0.f : (float)(1.0 / (2.0 * (double)sigma_s * (double)sigma_s));
+  a.S_true = S;
+  for (int z = -kMaxTapRadius; z <= kMaxTapRadius; ++z) {   // the forward's taps
+    float g = 0.f;
+    if (z >= -S && z <= S)
+      g = a.box ? 1.f : (float)exp(-(double)z * z / (2.0 * (double)sigma_s * (double)sigma_s));
+    a.taps[kMaxTapRadius + z] = make_float2(g, g);
+  }
+  a.eta_thr = 0.f;
+  a.narrow = 0;
+  a.out = nullptr;
+  a.zeta = nullptr;
+  a.eta = nullptr;
+  a.cout = cout;
+  a.k_begin = k_begin;
+  a.k_end = k_end;
+  a.c_only = 1;
+  if (Sc <= 8) return conv_dispatch_a(Sc, a, st);
+  if (Sc <= 16) return conv_dispatch_b(Sc, a, st);
+  return conv_dispatch_c(Sc, a, st);
 }
 
 }  // namespace nyf

@@ -37,7 +37,10 @@ struct ConvArgs {
   float* zeta;              // N x n, when they are split
   float* eta;               // N
   int narrow;               // FP32 kernel: 32 x 64 tiles instead of 32 x 96 (S <= 16)
-  float* cout;              // K (n + 1) planes C_kq (plane k (n + 1) + q) for the backward pass, or NULL
+  float* cout;              // convolved planes C_kq for the backward pass, or NULL: plane
+                            // (k - k_begin) (n + 1) + q for the modes k_begin <= k < k_end
+  int k_begin, k_end;       // modes processed (k_end is capped at the kept planes)
+  int c_only;               // recompute C only: no combine, nothing else is written
   float2 taps[2 * NYF_MAX_S + 1];   // (g(z), g(z)) for z = -32..32, zero beyond the true radius
 };
 
@@ -150,10 +153,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
   const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
   const int q0 = blockIdx.z * NQ;
   const int n = a.n;
-  const int r = a.state->planes;
+  const int kb = a.k_begin;
+  const int r = min(a.k_end, a.state->planes);   // modes kb <= k < r
 
   // Image planes of this CTA's quantities (zero outside the image and for the
-  // denominator quantity), then phi_0; both asynchronous.
+  // denominator quantity), then phi_kb; both asynchronous.
   for (int e = tid; e < NQ * HH * HW; e += kConvThreads) {
     const int qi = e / (HH * HW);
     const int rem = e - qi * (HH * HW);
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
     const bool in = c < n && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
     cp_async4(F + qi * PLANE + yy * PS + xx, in ? a.f + ((int64_t)gy * a.W + gx) * n + c : a.f, in);
   }
-  if (r > 0) stage_phi<S, WIDE>(a, PB, 0, ty0, tx0);
+  if (kb < r) stage_phi<S, WIDE>(a, PB, kb, ty0, tx0);
   cp_async_commit();
 
   const float2* g = a.taps + (kMaxTapRadius - S);   // (g, g) pairs, from the constant bank
@@ -178,18 +182,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
   const int vx = tid % HW, vy0 = (tid / HW) * RV;
   const bool vactive = tid < (TH / RV) * HW;     // one vertical task per thread (or none)
 
-  for (int k = 0; k < r; ++k) {
+  for (int k = kb; k < r; ++k) {
     // Prefetch phi_{k+1} into the other buffer while phi_k is consumed.  The
     // buffer was last read in iteration k-1, which ended with a barrier.
     if (k + 1 < r) {
-      stage_phi<S, WIDE>(a, PB + ((k + 1) & 1) * PLANE, k + 1, ty0, tx0);
+      stage_phi<S, WIDE>(a, PB + ((k + 1 - kb) & 1) * PLANE, k + 1, ty0, tx0);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const float* P = PB + (k & 1) * PLANE;
+    const float* P = PB + ((k - kb) & 1) * PLANE;
 #pragma unroll
     for (int pi = 0; pi < NP; ++pi) {
       const int qa = q0 + 2 * pi, qb = qa + 1;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
           acc[pi][j] = __ffma2_rn(f2(p, p), hb[j], acc[pi][j]);
         }
         if (a.cout && ty0 + hy < a.H) {          // keep C_kq for the backward pass
-          float* ca = a.cout + ((int64_t)k * (n + 1) + qa) * a.N + (int64_t)(ty0 + hy) * a.W + tx0 + hx0;
+          float* ca = a.cout + ((int64_t)(k - kb) * (n + 1) + qa) * a.N + (int64_t)(ty0 + hy) * a.W + tx0 + hx0;
           store_pair_row<RH>(ca, b_none ? nullptr : ca + a.N, hb, a.W - (tx0 + hx0));
         }
         __syncthreads();
@@ -246,6 +250,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
     }
   }
   cp_async_wait<0>();
+  if (a.c_only) return;
 
   // Epilogue: g_hat = zeta / eta (fused) or zeta, eta to memory (split).
   const int y = ty0 + hy;

@@ -79,6 +79,7 @@ struct Bars {
   uint64_t gh_ready;                  // Gh' written to tensor memory
   uint64_t d2_full[2], d2_empty[2];   // D2 slot written / read by the epilogue
   uint64_t pc_done[2];                // phi buffer's tile pixels copied by the epilogue
+  uint64_t phi_ready[2];              // phi_k has landed in buffer k & 1 (builders waited for it)
   uint64_t drain_h, drain_v;          // all products of an issuer complete (end of the kernel)
 };
 
@@ -218,6 +219,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
       umma::mbar_init(&bars.d2_full[s], 1);
       umma::mbar_init(&bars.d2_empty[s], 128);
       umma::mbar_init(&bars.pc_done[s], 128);
+      umma::mbar_init(&bars.phi_ready[s], 1);
     }
     umma::mbar_init(&bars.d1_full, 1);
     umma::mbar_init(&bars.d1_empty, 128);
@@ -248,6 +250,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
         else cp_async_wait<0>();
         builders_sync();
         pbuf = k & 1;
+        // every builder's copy of phi_k is complete: the epilogue may read the buffer
+        if (bt == 0) bar_arrive(&bars.phi_ready[pbuf]);
       }
       bool okw = true;
       if (u > 0) okw = umma::mbar_wait(&bars.q_empty[s], (u - 1) & 1, kWait);
@@ -405,8 +409,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
     for (int t = 0; t < T; ++t) {
       const int k = t / nq, q = t - k * nq, s = t & 1, u = t >> 1;
       if (q == 0) {                     // phi_k at this lane's pixels (FP32), from the builders'
-        // buffer: it holds phi_k from the build of (k, 0), which preceded D2(k, 0), until the
-        // builders see pc_done for it
+        // buffer: it holds phi_k once the builders signal phi_ready (their asynchronous
+        // copies of it are complete) until they see pc_done for it
+        const bool okp = umma::mbar_wait(&bars.phi_ready[k & 1], (k >> 1) & 1, kWait);
+        if (!__all_sync(0xffffffffu, okp) || abort_flag) { abort_flag = 1; fine = false; break; }
         const float* src = P + (k & 1) * (C::PPLANE / 4) + (SB + kTH - 1) * C::PSF + SB + (kTW - 1) - xp;
 #pragma unroll 8
         for (int yp = 0; yp < kTH; ++yp) pcs[yp * kTW + xp] = src[-yp * C::PSF];

@@ -4,8 +4,10 @@
 //   E_m(x)   = exp(-||p_x - mu_m||^2 / (2 sigma_r^2))       (column x of B, Eq. (11))
 //   phi_k(x) = sum_m E_m(x) W_hat[m][k]  =  sqrt(alpha_k) v_k(x)   (Eq. (12))
 // Distances are taken as direct FP32 differences (no norm expansion), exp is
-// CUDA's expf.  Output planes are planar (plane k at phi + k*N) so that the
-// convolution stage reads them coalesced.  The NLM variant forms the
+// CUDA's expf.  Guides of dimension rho >= 16 go to the tensor-core kernel of
+// features_tc.cu instead (the contraction over rho is deep enough to be one).
+// Output planes are planar (plane k at phi + k*N) so that the convolution
+// stage reads them coalesced.  The NLM variant forms the
 // (2r+1)^2 x n patch guide in shared memory from an image tile (reflect-101
 // border) instead of reading a stored guide.
 #include "nyf_internal.cuh"
@@ -269,6 +271,8 @@ cudaError_t nlm_k(const float* f, int H, int W, int n, int r, const float* lm, i
 cudaError_t launch_features(const float* guide, int64_t N, int rho, const float* landmarks, int K,
                             float sigma_r, const float* what, const DevState* state, void* phi,
                             bool bf16, cudaStream_t st) {
+  if (rho >= kFeaturesTcMinRho)   // a contraction deep enough for the tensor cores
+    return launch_features_tc(guide, N, rho, landmarks, K, sigma_r, what, state, phi, bf16, st);
   const float inv2s2 = (float)(1.0 / (2.0 * (double)sigma_r * (double)sigma_r));
   return bf16 ? features_k<true>(guide, N, rho, landmarks, K, inv2s2, what, state, phi, st)
               : features_k<false>(guide, N, rho, landmarks, K, inv2s2, what, state, phi, st);
@@ -277,6 +281,8 @@ cudaError_t launch_features(const float* guide, int64_t N, int rho, const float*
 cudaError_t launch_features_nlm(const float* f, int H, int W, int n, int r, const float* landmarks,
                                 int K, float sigma_r, const float* what, const DevState* state,
                                 void* phi, bool bf16, cudaStream_t st) {
+  if ((2 * r + 1) * (2 * r + 1) * n >= kFeaturesTcMinRho)
+    return launch_features_nlm_tc(f, H, W, n, r, landmarks, K, sigma_r, what, state, phi, bf16, st);
   const float inv2s2 = (float)(1.0 / (2.0 * (double)sigma_r * (double)sigma_r));
   return bf16 ? nlm_k<true>(f, H, W, n, r, landmarks, K, inv2s2, what, state, phi, st)
               : nlm_k<false>(f, H, W, n, r, landmarks, K, inv2s2, what, state, phi, st);
@@ -284,6 +290,7 @@ cudaError_t launch_features_nlm(const float* f, int H, int W, int n, int r, cons
 
 size_t features_nlm_smem_bytes(int K, int n, int r) {
   const int rho = (2 * r + 1) * (2 * r + 1) * n;
+  if (rho >= kFeaturesTcMinRho) return features_tc_smem_bytes(rho, K, n, r);
   const int TS = kNlmTile + 2 * r;
   return sizeof(float) * ((size_t)K * rho + (size_t)K * kpad(K) + (size_t)TS * TS * n);
 }

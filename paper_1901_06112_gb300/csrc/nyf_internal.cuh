@@ -47,6 +47,7 @@ struct WsShape {
   bool gather;      // k-means rows are gathered (subsample or NLM patches)
   bool bwd;         // regions of the backward pass (saved convolutions, adjoints, partials)
   bool iir;         // recursive-Gaussian planes (omega_v * (phi_k f_c), K (n + 1) planes)
+  bool recompute;   // backward recomputes C_kq: room for kRecomputeModes modes' planes only
 };
 
 WsLayout ws_layout(const WsShape& s);
@@ -91,6 +92,15 @@ cudaError_t launch_features_nlm(const float* f, int H, int W, int n, int r, cons
                                 int K, float sigma_r, const float* what, const DevState* state,
                                 void* phi, bool bf16, cudaStream_t st);
 size_t features_nlm_smem_bytes(int K, int n, int r);
+// Tensor-core (tcgen05) features for guides of dimension rho >= kFeaturesTcMinRho.
+constexpr int kFeaturesTcMinRho = 16;
+cudaError_t launch_features_tc(const float* guide, int64_t N, int rho, const float* landmarks,
+                               int K, float sigma_r, const float* what, const DevState* state,
+                               void* phi, bool bf16, cudaStream_t st);
+cudaError_t launch_features_nlm_tc(const float* f, int H, int W, int n, int r,
+                                   const float* landmarks, int K, float sigma_r, const float* what,
+                                   const DevState* state, void* phi, bool bf16, cudaStream_t st);
+size_t features_tc_smem_bytes(int rho, int K, int n, int r);
 cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void* phi, bool bf16,
                                 int tile, int spatial, float sigma_s, int S, DevState* state,
                                 float* out, float* eta_out, float* zeta_ws, float* cout,
@@ -101,10 +111,20 @@ cudaError_t launch_iir_combine(const float* f, int H, int W, int n, const float*
                                float sigma_s, DevState* state, float* out, float* eta_out,
                                float* zeta_ws, float* ybuf, cudaStream_t st);
 bool conv_split(int S, int n);
+// Adjoint convolutions of the modes k_begin <= k < k_end; cbuf holds their planes
+// C_kq (plane (k - k_begin) (n + 1) + q).  The chunk with k_begin == 0 also forms the
+// adjoint planes; later chunks add into grad_f and the sigma_s partials.
 cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spatial, float sigma_s,
                             int S, const void* phi, bool bf16, const float* eta, const float* out,
                             const float* grad_out, const float* cbuf, float* adj, float* grad_f,
-                            float* dphi, float* spart, const DevState* state, cudaStream_t st);
+                            float* dphi, float* spart, const DevState* state, cudaStream_t st,
+                            int k_begin, int k_end);
+// C_kq = omega * (phi_k f_q) of the modes k_begin <= k < k_end into cout (plane
+// (k - k_begin) (n + 1) + q), with the forward's FP32 kernel and nothing else written.
+cudaError_t launch_conv_recompute(const float* f, int H, int W, int n, const void* phi, bool bf16,
+                                  int spatial, float sigma_s, int S, int k_begin, int k_end,
+                                  DevState* state, float* cout, cudaStream_t st);
+constexpr int kRecomputeModes = NYF_RECOMPUTE_MODES;   // modes whose planes the recompute backward keeps at once
 cudaError_t launch_bwd_features(const float* f, const float* guide, int H, int W, int n, int rho,
                                 const float* landmarks, int K, float sigma_r, int S,
                                 const float* what, const float* dphi, float* grad_f,

@@ -32,7 +32,9 @@ class Params:
     patch_radius: int = 0          # NLM patch radius
     sample_frac: float = 1.0
     conv_tile: str = "auto"        # "auto" | "wide" | "narrow" | "tensor"
-    save_for_backward: bool = False  # forward keeps the convolved planes for blf_backward
+    save_for_backward: bool = False  # forward keeps what blf_backward reads
+    backward_mode: str = "planes"  # "planes": keep the K (n+1) convolved planes;
+    #                                "recompute": the backward convolves them again (low memory)
 
     def c(self) -> L.NyfParams:
         return L.NyfParams(float(self.sigma_s), float(self.sigma_r), int(self.K),
@@ -44,7 +46,8 @@ class Params:
                            int(self.patch_radius), float(self.sample_frac),
                            {"auto": L.TILE_AUTO, "wide": L.TILE_WIDE, "narrow": L.TILE_NARROW,
                             "tensor": L.TILE_TENSOR}[self.conv_tile],
-                           1 if self.save_for_backward else 0)
+                           0 if not self.save_for_backward else
+                           {"planes": 1, "recompute": 2}[self.backward_mode])
 
     def for_backward(self) -> "Params":
         """A copy whose forward keeps what the backward pass reads."""

@@ -41,15 +41,18 @@ def _case(H, W, K, seed, rho=None):
     return f, g, mu, G
 
 
+@pytest.mark.parametrize("mode", ["planes", "recompute"])
 @pytest.mark.parametrize("H,W,K,sigma_s,sigma_r", [(40, 36, 5, 2.0, 45.0), (33, 70, 8, 3.3, 60.0),
-                                                   (17, 19, 3, 1.4, 80.0)])
-def test_blf_backward_matches_oracle(nyf, H, W, K, sigma_s, sigma_r):
+                                                   (17, 19, 3, 1.4, 80.0), (45, 38, 9, 2.5, 50.0)])
+def test_blf_backward_matches_oracle(nyf, H, W, K, sigma_s, sigma_r, mode):
+    # mode "recompute": C_kq convolved again in chunks of 4 modes (K = 5, 9: a ragged last chunk)
     f, _, mu, G = _case(H, W, K, 100 + H)
     sr, ss = float(np.float32(sigma_r)), float(np.float32(sigma_s))
     S = int(math.ceil(3 * ss))
     ref = gr.vjp(f, f, mu, sr, ss, S, 1e-7, G, guide_is_image=True)
-    res = nyf.blf_vjp(cuda(f), nyf.Params(sigma_s=ss, sigma_r=sr, K=K), cuda(G), landmarks=cuda(mu))
-    r, _ = report(f"grad f {H}x{W} K={K}", res["df"].cpu().numpy(), ref["df"])
+    res = nyf.blf_vjp(cuda(f), nyf.Params(sigma_s=ss, sigma_r=sr, K=K, backward_mode=mode), cuda(G),
+                      landmarks=cuda(mu))
+    r, _ = report(f"grad f {H}x{W} K={K} {mode}", res["df"].cpu().numpy(), ref["df"])
     assert r < GRAD_TOL
     for nm in ("dsigma_r", "dsigma_s"):
         rel = abs(res[nm] - ref[nm]) / max(abs(ref[nm]), 1e-12)
@@ -70,18 +73,40 @@ def test_joint_guide_backward_matches_oracle(nyf):
     assert abs(res["dsigma_s"] - ref["dsigma_s"]) <= GRAD_TOL * abs(ref["dsigma_s"])
 
 
-def test_many_channels_backward(nyf):
+@pytest.mark.parametrize("mode", ["planes", "recompute"])
+def test_many_channels_backward(nyf, mode):
     # n = 7: quantities split over CTAs (dL/dphi accumulated across them)
     f = synth.hyperspectral(24, 26, 7, 3, 6.0, 0.02, 9) * 255.0
     g = synth.voronoi_colour(24, 26, 6, 5.0, 10)
     mu = g.reshape(-1, 3)[rng.distinct_indices(2, 5, 24 * 26)].astype(np.float32)
     G = np.random.default_rng(3).normal(size=f.shape).astype(np.float32)
     ref = gr.vjp(f, g, mu, 50.0, 1.5, 5, 1e-7, G)
-    res = nyf.blf_vjp(cuda(f), nyf.Params(sigma_s=1.5, sigma_r=50.0, K=5), cuda(G), guide=cuda(g),
-                      landmarks=cuda(mu))
-    r1, _ = report("n=7 grad f", res["df"].cpu().numpy(), ref["df"])
-    r2, _ = report("n=7 grad guide", res["dp"].cpu().numpy(), ref["dp"])
+    res = nyf.blf_vjp(cuda(f), nyf.Params(sigma_s=1.5, sigma_r=50.0, K=5, backward_mode=mode),
+                      cuda(G), guide=cuda(g), landmarks=cuda(mu))
+    r1, _ = report(f"n=7 grad f {mode}", res["df"].cpu().numpy(), ref["df"])
+    r2, _ = report(f"n=7 grad guide {mode}", res["dp"].cpu().numpy(), ref["dp"])
     assert r1 < GRAD_TOL and r2 < GRAD_TOL
+    for nm in ("dsigma_r", "dsigma_s"):
+        assert abs(res[nm] - ref[nm]) <= GRAD_TOL * abs(ref[nm])
+
+
+def test_recompute_mode_workspace_and_agreement(nyf):
+    # the recompute workspace holds 4 modes' planes instead of K; the gradients agree
+    # with the saved-planes backward to FP32 rounding (the same arithmetic, summed in
+    # chunks of modes)
+    f, _, mu, G = _case(96, 130, 11, 61)
+    P = nyf.Params(sigma_s=3.0, sigma_r=40.0, K=11)
+    Pp, Pr = P.for_backward(), nyf.Params(**{**P.__dict__, "backward_mode": "recompute"}).for_backward()
+    wp = nyf.workspace_size(96, 130, 3, 3, Pp)
+    wr = nyf.workspace_size(96, 130, 3, 3, Pr)
+    assert wp - wr >= (11 - 4) * 4 * 96 * 130 * 4
+    a = nyf.blf_vjp(cuda(f), Pp, cuda(G), landmarks=cuda(mu))
+    b = nyf.blf_vjp(cuda(f), Pr, cuda(G), landmarks=cuda(mu))
+    assert torch.equal(a["out"], b["out"])
+    r, _ = report("recompute vs planes grad f", b["df"].cpu().numpy(), a["df"].cpu().numpy())
+    assert r < 1e-5
+    for nm in ("dsigma_r", "dsigma_s"):
+        assert abs(a[nm] - b[nm]) <= 1e-5 * abs(a[nm])
 
 
 def test_sigma_gradients_match_finite_differences(nyf):

@@ -138,7 +138,14 @@ def test_workload_64_images_against_oracle(nyf, workload64, precision):
     outs, gfs = bt.unpack(out), bt.unpack(gf)
 
     # the graph replay equals one call per image with the same landmarks, bitwise,
-    # on every image of the workload, forward and backward
+    # on every image of the workload, forward and backward.  NaN compares equal to
+    # NaN here: where every feature of a pixel underflows (sigma_r = 11 with 16
+    # landmarks for 40 random colours), eta_hat = 0 and g_hat = 0 / 0, which Eq. (15)
+    # allows and the filter does not clamp; both calls must agree on those pixels too.
+    def same(a, b):
+        na, nb = torch.isnan(a), torch.isnan(b)
+        return torch.equal(na, nb) and torch.equal(a.masked_fill(na, 0), b.masked_fill(nb, 0))
+
     for b, w in enumerate(batch):
         Pb = nyf.Params(sigma_s=ss[b], sigma_r=sr[b], K=16, kmeans_iters=10,
                         precision=precision, save_for_backward=True)
@@ -146,9 +153,11 @@ def test_workload_64_images_against_oracle(nyf, workload64, precision):
         ws = nyf.make_workspace(w.H, w.W, 3, 3, Pb)
         ob = nyf.blf(fb, Pb, landmarks=lm[b].contiguous(), ws=ws)
         bb = nyf.blf_backward(fb, Pb, ob, torch.from_numpy(Gs[b]).cuda(), ws)
-        assert torch.equal(outs[b], ob), b
-        assert torch.equal(gfs[b], bb.grad_f), b
-        assert torch.equal(gs[b], bb.grad_sigma), b
+        assert same(outs[b], ob), b
+        assert same(gfs[b], bb.grad_f), b
+        assert same(gs[b], bb.grad_sigma), b
+        if torch.isnan(ob).any():           # only where the features vanish
+            assert bt.stats(b)["eta_small"] > 0, b
         del ws
 
     # the checked images against the FP64 oracle: sampled output pixels, and the

@@ -121,9 +121,11 @@ def test_nlm_768x512_sampled_parity(nyf):
     assert st["status"] == 0 and abs(st["qerr"] - info["e"]) <= 1e-3 * info["e"]
 
 
-def test_colour_1920x1080_backward_vs_oracle_on_a_window(nyf, hd):
+@pytest.mark.parametrize("mode", ["planes", "recompute"])
+def test_colour_1920x1080_backward_vs_oracle_on_a_window(nyf, hd, mode):
     # G = dL/d g_hat is nonzero only on a window R; g_hat on R depends only on the
     # image inside R grown by S, so the oracle gradient on that crop is exact.
+    # mode "recompute": the low-memory backward (C_kq convolved again, 4 modes at a time).
     from oracle import grad as gr
     w, mu, _ = hd
     S = w.radius
@@ -131,8 +133,8 @@ def test_colour_1920x1080_backward_vs_oracle_on_a_window(nyf, hd):
     G = np.zeros(w.f.shape, np.float32)
     G[y0:y0 + h, x0:x0 + h] = np.random.default_rng(7).normal(size=(h, h, 3))
     sr = float(np.float32(w.sigma_r))
-    res = nyf.blf_vjp(cuda(w.f), nyf.Params(sigma_s=w.sigma_s, sigma_r=sr, K=w.K), cuda(G),
-                      landmarks=cuda(mu))
+    res = nyf.blf_vjp(cuda(w.f), nyf.Params(sigma_s=w.sigma_s, sigma_r=sr, K=w.K, backward_mode=mode),
+                      cuda(G), landmarks=cuda(mu))
     c0, c1 = (y0 - S, y0 + h + S), (x0 - S, x0 + h + S)
     crop = w.f[c0[0]:c0[1], c1[0]:c1[1]]
     ref = gr.vjp(crop, crop, mu, sr, w.sigma_s, S, 1e-7, G[c0[0]:c0[1], c1[0]:c1[1]],

@@ -116,6 +116,45 @@ def test_features_match_oracle(nyf, K, sigma_r, rho):
     assert rr < 1e-5
 
 
+def _tc_guide(kind, seed):
+    """Guides of dimension >= 16 (the tensor-core features path) and their sigma_r."""
+    from oracle import guide as gd
+    from oracle import pca as pc
+    if kind == "patch75":             # 5x5x3 NLM patches, 37 x 41 (N = 1517: ragged last tile)
+        g = synth.voronoi_colour(37, 41, 20, 20.0, seed, ramp=0.1)
+        return gd.patch_guide(g.astype(np.float64), 2).reshape(-1, 75), 20.0 * np.sqrt(75.0)
+    if kind == "pca25":               # 7x7x3 patches projected on 25 principal directions
+        g = synth.voronoi_colour(40, 36, 20, 20.0, seed, ramp=0.1)
+        return pc.pca_guide(g.astype(np.float64), 3, 25)[0].reshape(-1, 25), 424.0
+    if kind == "rho16":               # N = 117 < one 128-pixel tile
+        return synth.random_image(9, 13, 16, seed, R=1.0).reshape(-1, 16), 0.9
+    if kind == "rho47":
+        return synth.hyperspectral(25, 40, 47, 5, 8.0, 0.02, seed).reshape(-1, 47), 0.2
+    if kind == "rho160":              # the largest guide dimension
+        return synth.hyperspectral(20, 15, 160, 4, 6.0, 0.02, seed).reshape(-1, 160), 0.4
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind,K", [("patch75", 32), ("pca25", 31), ("rho16", 5), ("rho47", 17),
+                                    ("rho160", 64), ("rho160", 1)])
+def test_features_tensor_cores_match_oracle(nyf, kind, K):
+    # rho >= 16: distances and E W_hat on the tensor cores (three-term bf16 split)
+    X, sigma_r = _tc_guide(kind, 40 + K)
+    X = np.ascontiguousarray(X, np.float32)
+    mu, _ = oracle_landmarks(X, K, 5, 13)
+    sigma_r = float(np.float32(sigma_r))
+    phi, rank, alphas = nyf.features(cuda(X), cuda(mu), sigma_r, 1e-7)
+    _, alpha_o, _, keep = ny.spectral_step(mu.astype(np.float64), sigma_r, 1e-7)
+    assert int(rank.cpu()) == keep.size
+    phi_o, _, _ = ny.features_symmetric(X.astype(np.float64), mu.astype(np.float64), sigma_r, 1e-7)
+    rr, _ = report(f"tensor-core features {kind} K={K} N={X.shape[0]}", phi.cpu().numpy().T, phi_o)
+    assert rr < 1e-5
+    # bfloat16 storage of the same features: each value rounded by at most 2^-8
+    pb, _, _ = nyf.features(cuda(X), cuda(mu), sigma_r, 1e-7, precision="bf16")
+    rb, _ = report(f"tensor-core features {kind} K={K} bf16", pb.float().cpu().numpy().T, phi_o)
+    assert rb < 2.0 ** -8
+
+
 # ---------------------------------------------------------------- filters
 
 def _params(nyf, w, **kw):
