@@ -148,6 +148,44 @@ def cpu_baseline_obj(backward=True):
                       f"{CPU_SAMPLE[1]} crop of the workload, one thread, {sec:.1f} s"}
 
 
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_fp32_baseline(wl, reps=3):
+    """The FP32 C++/OpenMP filter (same algorithm as the GPU path, forward) on the host:
+    the whole workload with every core, and a 512 x 512 crop with one thread; median of
+    `reps` runs each, megapixels/s."""
+    from oracle import cpu_build
+    lib = cpu_build.load()
+    res = {}
+    for label, f, threads in (("all_cores", wl.f, 0), ("one_thread", wl.f[:512, :512], 1)):
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            _, code = cpu_build.blf(lib, f, wl.sigma_s, wl.sigma_r, wl.K, wl.kmeans_iters, wl.seed,
+                                    threads=threads)
+            ts.append(time.perf_counter() - t0)
+            if code != 0:
+                raise RuntimeError(f"cpu baseline status {code}")
+        sec = float(np.median(ts))
+        res[label] = {"value": f.shape[0] * f.shape[1] / 1e6 / sec, "seconds": sec,
+                      "threads": threads if threads else lib.nyf_cpu_threads(),
+                      "pixels": f.shape[0] * f.shape[1]}
+    res.update({"unit": "megapixels/s", "kind": "fp32 C++/OpenMP, forward (k-means 10 iters, "
+                "eig, features, FIR convolutions, combine)", "cpu": cpu_model(),
+                "os_cpu_count": os.cpu_count()})
+    return res
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -822,6 +860,10 @@ def main():
                 line["cpu_baseline"] = cpu_baseline_obj(backward=fwdbwd)
             except Exception as ex:  # the oracle leg must not hide the GPU number
                 line["cpu_baseline"] = {"error": str(ex)[:200]}
+            try:
+                line["cpu_baseline_fp32"] = cpu_fp32_baseline(wl)
+            except Exception as ex:
+                line["cpu_baseline_fp32"] = {"error": str(ex)[:200]}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
