@@ -493,7 +493,7 @@ def config_line(nyf, lib, w, golden, precision, fwdbwd, steps, flush, stream):
     counts = stage_counts(N, n, rho, planes, 2 * w.radius + 1, w.kmeans_iters, Ns, fwdbwd,
                           conv_tensor=precision == "bf16" and w.radius <= 16 and n <= 3,
                           nlm_r=w.patch_radius)
-    sm = {k: v for k, v in zip(STAGES, stages[:6]) if v is not None}
+    sm = {k: v for k, v in zip(STAGES, stages[:6 if fwdbwd else 4]) if v is not None}
     line = {"workload": w.name, "mode": "fwd+bwd" if fwdbwd else "fwd", "precision": precision,
             "value": N / 1e6 / (ms / 1e3), "unit": "megapixels/s", "ms_per_step": ms,
             "stages_ms": sm, "status": st["status"], "rank_r": st["rank"],
