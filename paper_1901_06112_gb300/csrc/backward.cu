@@ -38,6 +38,13 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
   float* mu = Wsm + K * KP;                 // K x rho
   float* Es = mu + ((K * rho + 3) & ~3);    // kFbThreads x KB
   float* Ds = Es + kFbThreads * KB;         // kFbThreads x KB
+  // RB == 0 (rho > 32): this thread's guide row and its dL/dp accumulate in shared
+  // memory (row stride rho | 1: odd, so a warp's rows fall in distinct banks).
+  // RB < 0 (that does not fit): the row is read from global memory and dL/dp
+  // accumulated there, one landmark at a time.
+  const int RS = rho | 1;
+  float* Xs = Ds + kFbThreads * KB;         // kFbThreads x RS (RB == 0 only)
+  float* Ps = Xs + kFbThreads * RS;         // kFbThreads x RS (RB == 0 only)
   const int tid = threadIdx.x;
   const int r = state->planes;
   for (int e = tid; e < K * KP; e += blockDim.x) {
@@ -65,6 +72,13 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
       x[d] = (RB > 0 && d < rho) ? __ldg(p + d) : 0.f;
       dp[d] = 0.f;
     }
+    float* xs = Xs + tid * RS;
+    float* ps = Ps + tid * RS;
+    if (RB == 0)
+      for (int d = 0; d < rho; ++d) {
+        xs[d] = __ldg(p + d);
+        ps[d] = 0.f;
+      }
     float g[KB];                                   // dPhi of this pixel
 #pragma unroll
     for (int k = 0; k < KB; ++k) g[k] = (valid && k < r) ? dphi[(int64_t)k * N + i] : 0.f;
@@ -79,6 +93,11 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
             const float t = x[d] - c[d];
             d2 = fmaf(t, t, d2);
           }
+      } else if (RB == 0) {
+        for (int d = 0; d < rho; ++d) {
+          const float t = xs[d] - c[d];
+          d2 = fmaf(t, t, d2);
+        }
       } else {
         for (int d = 0; d < rho; ++d) {
           const float t = __ldg(p + d) - c[d];
@@ -104,6 +123,8 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
 #pragma unroll
         for (int d = 0; d < RX; ++d)
           if (d < rho) dp[d] = fmaf(dDm, 2.f * (x[d] - c[d]), dp[d]);
+      } else if (RB == 0) {
+        for (int d = 0; d < rho; ++d) ps[d] = fmaf(dDm, 2.f * (xs[d] - c[d]), ps[d]);
       } else if (valid) {
         float* dst = dguide + i * rho;
         for (int d = 0; d < rho; ++d) {
@@ -114,11 +135,15 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
       Es[tid * KB + m] = e;
     }
     for (int m = K; m < KB; ++m) Es[tid * KB + m] = 0.f;
-    if (RB > 0 && valid) {
+    if (valid) {
       float* dst = dguide + i * rho;
+      if (RB > 0) {
 #pragma unroll
-      for (int d = 0; d < RX; ++d)
-        if (d < rho) dst[d] = add_into ? dst[d] + dp[d] : dp[d];
+        for (int d = 0; d < RX; ++d)
+          if (d < rho) dst[d] = add_into ? dst[d] + dp[d] : dp[d];
+      } else if (RB == 0) {
+        for (int d = 0; d < rho; ++d) dst[d] = add_into ? dst[d] + ps[d] : ps[d];
+      }
     }
 #pragma unroll
     for (int k = 0; k < KB; ++k) Ds[tid * KB + k] = g[k];
@@ -306,7 +331,8 @@ cudaError_t fb_launch(const float* guide, int64_t N, int rho, const float* lm, i
                       const float* what, const DevState* state, const float* dphi, float* dguide,
                       int add_into, float* gw_part, float* sr_part, cudaStream_t st) {
   const size_t smem = sizeof(float) * ((size_t)K * kpad4(K) + (size_t)((K * rho + 3) & ~3) +
-                                       (size_t)2 * kFbThreads * KB);
+                                       (size_t)2 * kFbThreads * KB +
+                                       (RB == 0 ? (size_t)2 * kFbThreads * (rho | 1) : 0));
   cudaError_t e = cudaFuncSetAttribute(k_features_bwd<KB, RB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -324,8 +350,16 @@ cudaError_t fb_rb(const float* guide, int64_t N, int rho, const float* lm, int K
   if (rho <= 4)
     return fb_launch<KB, 4>(guide, N, rho, lm, K, inv2s2r, what, state, dphi, dguide, add_into,
                             gw_part, sr_part, st);
-  return fb_launch<KB, 0>(guide, N, rho, lm, K, inv2s2r, what, state, dphi, dguide, add_into,
-                          gw_part, sr_part, st);
+  if (rho <= 32)
+    return fb_launch<KB, 32>(guide, N, rho, lm, K, inv2s2r, what, state, dphi, dguide, add_into,
+                             gw_part, sr_part, st);
+  const size_t rows = sizeof(float) * ((size_t)K * kpad4(K) + (size_t)((K * rho + 3) & ~3) +
+                                       (size_t)2 * kFbThreads * KB + (size_t)2 * kFbThreads * (rho | 1));
+  if (rows <= 227 * 1024)
+    return fb_launch<KB, 0>(guide, N, rho, lm, K, inv2s2r, what, state, dphi, dguide, add_into,
+                            gw_part, sr_part, st);
+  return fb_launch<KB, -1>(guide, N, rho, lm, K, inv2s2r, what, state, dphi, dguide, add_into,
+                           gw_part, sr_part, st);
 }
 
 }  // namespace

@@ -73,6 +73,25 @@ def test_joint_guide_backward_matches_oracle(nyf):
     assert abs(res["dsigma_s"] - ref["dsigma_s"]) <= GRAD_TOL * abs(ref["dsigma_s"])
 
 
+@pytest.mark.parametrize("rho,K", [(31, 16), (40, 8), (160, 64)])
+def test_deep_guide_backward_matches_oracle(nyf, rho, K):
+    # dL/dp for guides of dimension 31 (row in registers), 40 (row staged in shared
+    # memory) and 160 with K = 64 (row in global memory): the three paths of the
+    # features backward
+    f = synth.voronoi_colour(22, 27, 6, 8.0, 50 + rho)
+    g = synth.hyperspectral(22, 27, rho, 4, 6.0, 0.02, 60 + rho)
+    mu = g.reshape(-1, rho)[rng.distinct_indices(3, K, 22 * 27)].astype(np.float32)
+    G = np.random.default_rng(rho).normal(size=f.shape).astype(np.float32)
+    sr = float(np.float32(0.35 if rho < 100 else 0.8))
+    ref = gr.vjp(f, g, mu, sr, 1.5, 5, 1e-7, G)
+    res = nyf.blf_vjp(cuda(f), nyf.Params(sigma_s=1.5, sigma_r=sr, K=K), cuda(G), guide=cuda(g),
+                      landmarks=cuda(mu))
+    r1, _ = report(f"rho={rho} K={K} grad f", res["df"].cpu().numpy(), ref["df"])
+    r2, _ = report(f"rho={rho} K={K} grad guide", res["dp"].cpu().numpy(), ref["dp"])
+    assert r1 < GRAD_TOL and r2 < GRAD_TOL
+    assert abs(res["dsigma_r"] - ref["dsigma_r"]) <= GRAD_TOL * abs(ref["dsigma_r"])
+
+
 @pytest.mark.parametrize("mode", ["planes", "recompute"])
 def test_many_channels_backward(nyf, mode):
     # n = 7: quantities split over CTAs (dL/dphi accumulated across them)
