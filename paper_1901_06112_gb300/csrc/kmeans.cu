@@ -463,6 +463,22 @@ cudaError_t launch_draw_init(const float* X, int64_t N, int rho, int K, uint64_t
 cudaError_t launch_kmeans(const float* X, int64_t N, int rho, int K, int iters, float* centroids,
                           int32_t* labels, double* qerr_out, float* part, float* qpart,
                           DevState* state, cudaStream_t st) {
+  if (assign_tc_supported(rho, K)) {   // rows deep enough for the tensor cores
+    const int grid = assign_tc_grid(N);
+    for (int it = 0; it < iters; ++it) {
+      cudaError_t e = launch_assign_tc(grid, X, N, rho, K, centroids, nullptr, part, qpart, 1,
+                                       state, st);
+      if (e != cudaSuccess) return e;
+      k_update<<<K, 256, 0, st>>>(part, grid, rho, K, centroids);
+      count_launches(1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    cudaError_t e = launch_assign_tc(grid, X, N, rho, K, centroids, labels, part, qpart, 0, state, st);
+    if (e != cudaSuccess) return e;
+    k_qerr<<<1, 256, 0, st>>>(qpart, grid, qerr_out, state);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   const int grid = kmeans_grid(N, rho);
   for (int it = 0; it < iters; ++it) {
     cudaError_t e = assign_dispatch(grid, X, N, rho, K, centroids, nullptr, part, qpart, 1, st);

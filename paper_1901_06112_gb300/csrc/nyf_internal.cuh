@@ -79,6 +79,12 @@ cudaError_t launch_kmeans(const float* X, int64_t N, int rho, int K, int iters, 
 cudaError_t launch_sample_rows(const float* guide, int64_t N, int rho, int64_t Ns, uint64_t seed,
                                int64_t* idx, float* X, cudaStream_t st);
 size_t kmeans_smem_bytes(int K, int rho);
+// Tensor-core (tcgen05) assignment pass for rows of dimension 16..80 (kmeans_tc.cu).
+bool assign_tc_supported(int rho, int K);
+int assign_tc_grid(int64_t N);
+cudaError_t launch_assign_tc(int grid, const float* X, int64_t N, int rho, int K,
+                             const float* cent, int32_t* labels, float* part, float* qpart,
+                             int accumulate, DevState* state, cudaStream_t st);
 cudaError_t launch_nlm_sample(const float* f, int H, int W, int n, int r, int64_t Ns, uint64_t seed,
                               int64_t* idx, float* X, cudaStream_t st);
 cudaError_t launch_eig(const float* landmarks, int K, int rho, float sigma_r, double tau,

@@ -93,6 +93,34 @@ def test_kmeans_ten_iterations_objective(nyf):
     assert abs(float(qerr.cpu()) - e_o) <= 1e-3 * e_o
 
 
+@pytest.mark.parametrize("rho,K,N", [(31, 16, 1000), (75, 32, 3932), (25, 31, 777), (80, 64, 4200)])
+def test_kmeans_tensor_cores_match_oracle(nyf, rho, K, N):
+    # 16 <= rho <= 80: distances and per-cluster sums on the tensor cores (N not a
+    # multiple of the 128-row tile)
+    r = np.random.default_rng(rho + K)
+    C = r.uniform(0, 1, size=(K + 3, rho))
+    X = (C[r.integers(0, K + 3, size=N)] + r.normal(0, 0.08, size=(N, rho))).astype(np.float32)
+    init = rng.distinct_indices(7, K, N)
+    # one step: centroids equal the oracle's where the labels are unique
+    cent1, labels1, _ = nyf.kmeans(cuda(X), K, iters=1, init_idx=torch.from_numpy(init))
+    mu1, _, _, _ = km.kmeans(X.astype(np.float64), X[init].astype(np.float64), 1)
+    rr, _ = report(f"tensor-core kmeans 1 step rho={rho} K={K}", cent1.cpu().numpy(), mu1)
+    assert rr < 1e-6
+    # labels of the final centroids: the oracle's wherever its best distance is unique,
+    # within rounding of the best elsewhere
+    D = km.sq_dists(X.astype(np.float64), cent1.cpu().numpy().astype(np.float64))
+    srt = np.sort(D, axis=1)
+    unique = (srt[:, 1] - srt[:, 0]) > 1e-5 * (1.0 + srt[:, 0])
+    got = labels1.cpu().numpy()
+    assert np.array_equal(got[unique], np.argmin(D, axis=1)[unique])
+    assert np.all(D[~unique, got[~unique]] <= srt[~unique, 0] * (1 + 1e-5) + 1e-5)
+    # ten iterations: the objective
+    _, _, qerr = nyf.kmeans(cuda(X), K, iters=10, init_idx=torch.from_numpy(init))
+    _, _, e_o, _ = km.kmeans(X.astype(np.float64), X[init].astype(np.float64), 10)
+    print(f"[parity] tensor-core kmeans e: gpu={float(qerr.cpu()):.6e} oracle={e_o:.6e}")
+    assert abs(float(qerr.cpu()) - e_o) <= 1e-4 * e_o
+
+
 # ---------------------------------------------------------------- eig + features
 
 @pytest.mark.parametrize("K,sigma_r,rho", [(8, 30.0, 3), (32, 40.0, 3), (64, 0.15, 31), (1, 50.0, 3)])
