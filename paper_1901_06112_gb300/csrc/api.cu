@@ -47,7 +47,7 @@ WsLayout ws_layout(const WsShape& s) {
   L.dphi = take(s.bwd ? sizeof(float) * K * N : 0);
   L.gpart = take(s.bwd ? sizeof(float) * backward_gpart_floats(s.K) : 0);
   L.spart = take(s.bwd ? sizeof(float) * backward_spart_floats(s.H, s.W, s.n) : 0);
-  L.gw = take(s.bwd ? sizeof(double) * (2 * K * K + K) : 0);
+  L.gw = take(s.bwd ? sizeof(double) * (3 * K * K + K) : 0);   // G_W, Z, row dots, A o D2
   L.adj = take(s.bwd ? sizeof(float) * nq1 * N : 0);
   const size_t kc = s.recompute ? std::min(K, (size_t)kRecomputeModes) : K;
   L.cbuf = take(s.bwd ? sizeof(float) * kc * nq1 * N : 0);

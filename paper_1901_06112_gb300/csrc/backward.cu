@@ -209,8 +209,23 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
 // so Z (which does not depend on the incoming gradient) replaces three K^3
 // products after the reduction of G_W by one dot product per row.
 __global__ void __launch_bounds__(kMaxK)
-k_tail_z(int K, int rho, const float* __restrict__ lm, const float* __restrict__ what,
-         const double* __restrict__ A64, const DevState* __restrict__ state, double* __restrict__ Z) {
+k_tail_ad2(int K, int rho, const float* __restrict__ lm, const double* __restrict__ A64,
+           double* __restrict__ AD2) {
+  // (A o D2)[a][t] = A(a, t) ||mu_a - mu_t||^2, one row per CTA (FP64)
+  const int a = blockIdx.x, t = threadIdx.x;
+  if (t < K) {
+    double d2 = 0.0;
+    for (int d = 0; d < rho; ++d) {
+      const double u = (double)lm[a * rho + d] - (double)lm[t * rho + d];
+      d2 += u * u;
+    }
+    AD2[a * K + t] = A64[a * K + t] * d2;
+  }
+}
+
+__global__ void __launch_bounds__(kMaxK)
+k_tail_z(int K, const float* __restrict__ what, const double* __restrict__ AD2,
+         const DevState* __restrict__ state, double* __restrict__ Z) {
   __shared__ double Mrow[kMaxK], MX[kMaxK];
   const int i = blockIdx.x, t = threadIdx.x;
   const int r = state->planes;
@@ -222,14 +237,7 @@ k_tail_z(int K, int rho, const float* __restrict__ lm, const float* __restrict__
   __syncthreads();
   if (t < K) {
     double s = 0.0;
-    for (int a = 0; a < K; ++a) {
-      double d2 = 0.0;
-      for (int d = 0; d < rho; ++d) {
-        const double u = (double)lm[a * rho + d] - (double)lm[t * rho + d];
-        d2 += u * u;
-      }
-      s += Mrow[a] * A64[a * K + t] * d2;
-    }
+    for (int a = 0; a < K; ++a) s += Mrow[a] * AD2[a * K + t];
     MX[t] = s;
   }
   __syncthreads();
@@ -455,8 +463,10 @@ cudaError_t launch_bwd_features(const float* f, const float* guide, int H, int W
   float* sr_part = gpart + (size_t)kFbBlocks * K * K;
   double* Z = gw + (size_t)K * K;
   double* rowdot = Z + (size_t)K * K;
-  k_tail_z<<<K, kMaxK, 0, st>>>(K, rho, landmarks, what, eig_A64(eig_scratch), state, Z);
-  count_launches(1);
+  double* AD2 = rowdot + K;
+  k_tail_ad2<<<K, kMaxK, 0, st>>>(K, rho, landmarks, eig_A64(eig_scratch), AD2);
+  k_tail_z<<<K, kMaxK, 0, st>>>(K, what, AD2, state, Z);
+  count_launches(2);
   cudaError_t e;
   if (K <= 8) e = fb_rb<8>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);
   else if (K <= 16) e = fb_rb<16>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);

@@ -55,7 +55,7 @@ __host__ __device__ inline int pad16(int v) { return (v + 15) & ~15; }
 // Shared-memory layout (byte offsets) of one CTA.
 struct FtLayout {
   int rp, kp;                  // rho and K rounded up to 16
-  int a, b1, b2, c, bn, tile, total;
+  int a, b1, b2, c, bn, tile, poff, total;
 };
 
 __host__ __device__ inline FtLayout ft_layout(int rho, int K, int tile_floats) {
@@ -76,6 +76,8 @@ __host__ __device__ inline FtLayout ft_layout(int rho, int K, int tile_floats) {
   o += 4 * L.kp;                             // ||mu~_m||^2
   L.tile = o;
   o += 4 * tile_floats;                      // NLM image tile
+  L.poff = o;
+  o += tile_floats > 0 ? 4 * L.rp : 0;       // NLM: tile offset of each patch component
   L.total = (o + 127) & ~127;
   return L;
 }
@@ -121,6 +123,13 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_features_tc(const __grid_cons
   float* cen = reinterpret_cast<float*>(sm + L.c);
   float* bnorm = reinterpret_cast<float*>(sm + L.bn);
   float* tile = reinterpret_cast<float*>(sm + L.tile);
+  int* poff = reinterpret_cast<int*>(sm + L.poff);
+  if (NLM)   // component j = (dy side + dx) n + c sits at tile offset (dy TSX + dx) n + c
+    for (int d = tid; d < rho; d += kFtThreads) {
+      const int c = d % a.n, q = d / a.n;
+      const int dy = q / side, dx = q - dy * side;
+      poff[d] = (dy * TSX + dx) * a.n + c;
+    }
   const int a1_term = kFtRows * rp * 2, a2_term = kFtRows * kp * 2;
   const int b1_term = kp * rp * 2, b2_term = kp * kp * 2;
 
@@ -201,18 +210,15 @@ __global__ void __launch_bounds__(kFtThreads, 1) k_features_tc(const __grid_cons
       __syncthreads();
       const int ty = tid / kNlmTX, tx = tid % kNlmTX;
       if (ty0 + ty < a.H && tx0 + tx < a.W) pix = (int64_t)(ty0 + ty) * a.W + tx0 + tx;
-      // component j = (dy * side + dx) * n + c, read from the tile
+      // the patch components, read from the tile through the offset table
+      const float* tp = tile + (ty * TSX + tx) * a.n;
       for (int d0 = 0; d0 < rp; d0 += 8) {
         float v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int d = d0 + i;
           float x = 0.f;
-          if (pix >= 0 && d < rho) {
-            const int c = d % a.n, q = d / a.n;
-            const int dy = q / side, dx = q - dy * side;
-            x = tile[((ty + dy) * TSX + tx + dx) * a.n + c] - cen[d];
-          }
+          if (pix >= 0 && d < rho) x = tp[poff[d]] - cen[d];
           v[i] = x;
           anorm = fmaf(x, x, anorm);
         }
