@@ -771,6 +771,25 @@ def main():
                                     flush, stream, lib)
             extras["fwd"] = {"value": mp / (fwd_ms / 1e3), "ms_per_step": fwd_ms,
                              "unit": "megapixels/s", "precision": args.precision}
+        if fwdbwd and not iir:                    # the low-memory backward (C_kq recomputed)
+            Pr = make(args.precision, True)
+            Pr.backward_mode = "recompute"
+            wsr = nyf.make_workspace(H, W, n, n, Pr, dev)
+
+            def step_r():
+                nyf.blf(f_dev, Pr, out=out, ws=wsr)
+                nyf.blf_backward(f_dev, Pr, out, G, wsr, grads)
+            lib.nyf_set_timing(1)
+            for _ in range(2):
+                step_r()
+            r_ms, r_st = timed_steps(step_r, max(3, args.steps // 2), flush, stream, lib)
+            lib.nyf_set_timing(0)
+            extras["recompute_backward"] = {
+                "value": mp / (r_ms / 1e3), "ms_per_step": r_ms, "unit": "megapixels/s",
+                "bwd_conv_ms": r_st[4], "workspace_GB": wsr.nbytes / 1e9,
+                "workspace_GB_planes_kept": ws.nbytes / 1e9,
+                "mode": "fwd+bwd, C_kq convolved again 4 modes at a time"}
+            del wsr
         other = "bf16" if args.precision == "fp32" else "fp32"
         if iir:
             other = None

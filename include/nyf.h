@@ -142,6 +142,38 @@ nyf_status nyf_kmeans(const float* X, int64_t N, int rho, int K, int iters, uint
                       const int64_t* init_idx, float* centroids, int32_t* labels, double* qerr,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* ---- Strip processing: an image cut into horizontal strips (one per GPU, or
+ * one at a time on one GPU), each filtered with an S-row halo, with k-means
+ * run over all strips by exchanging per-cluster sums (Sec. III clustering:
+ * the Lloyd update is a mean, so it only needs the strips' sums and counts).
+ *
+ * nyf_draw_indices (host only, no GPU work): the k-means initial rows of an
+ * image of N rows, the first K distinct values of SplitMix64(seed) output mod N
+ * (the same draw as nyf_kmeans with init_idx == NULL), into out[0..K) (host
+ * int64).  Returns the number drawn (K, or fewer if the draw limit of 64 K +
+ * 4096 outputs was reached; 0 for invalid arguments). */
+int nyf_draw_indices(uint64_t seed, int64_t N, int K, int64_t* out);
+
+/* out (K x rho, device) = row idx[j] - row0 of X (N x rho, device) when
+ * 0 <= idx[j] - row0 < N, else zeros: a strip's share of the initial centroids
+ * (the strips' shares add up to the rows of the whole image).  idx: K device
+ * int64 (whole-image row numbers); row0: the strip's first row number. */
+nyf_status nyf_gather_rows(const float* X, int64_t N, int rho, int64_t row0, const int64_t* idx,
+                           int K, float* out, void* stream);
+
+/* One assignment pass of Lloyd's algorithm over the N x rho rows X against the
+ * K x rho centroids (nearest centroid, ties to the lowest index):
+ *   sums  K x (rho + 1) doubles (device, out): sums[j (rho + 1) + d] = the sum of
+ *         coordinate d over the rows assigned to j, sums[j (rho + 1) + rho] = their count
+ *   qerr  1 double (device, out): the sum of the rows' squared distances to their centroid.
+ * Sums are formed in a fixed order (bitwise reproducible).  ws as for nyf_kmeans. */
+nyf_status nyf_kmeans_partials(const float* X, int64_t N, int rho, int K, const float* centroids,
+                               double* sums, double* qerr, void* ws, size_t ws_bytes, void* stream);
+
+/* The update step from (all-reduced) sums: centroid j = sums[j][0..rho) / sums[j][rho],
+ * unchanged when the count is zero. */
+nyf_status nyf_kmeans_apply_sums(const double* sums, int K, int rho, float* centroids, void* stream);
+
 /* Nystrom per-pixel features (Eqs. (9)-(12)).  For landmarks mu (K x rho):
  * A(i,j) = kappa(mu_i, mu_j) is decomposed to FP64 accuracy (Eq. (10)),
  * modes with alpha_k > eig_rel_tol * alpha_max are kept (r of them), and for

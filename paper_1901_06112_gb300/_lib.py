@@ -78,6 +78,11 @@ _SIGNATURES.update({
     "nyf_batched_stats": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(NyfParams), C.c_int,
                                     C.POINTER(NyfStats), _P]),
     "nyf_iir_line_params": (C.c_int, [C.c_double, C.c_int, C.POINTER(C.c_float), C.c_int]),
+    "nyf_draw_indices": (C.c_int, [C.c_uint64, C.c_int64, C.c_int, C.POINTER(C.c_int64)]),
+    "nyf_gather_rows": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int64, _P, C.c_int, _P, _P]),
+    "nyf_kmeans_partials": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, _P, _P, _P, _P, C.c_size_t,
+                                      _P]),
+    "nyf_kmeans_apply_sums": (C.c_int, [_P, C.c_int, C.c_int, _P, _P]),
     "nyf_patch_pca_workspace_size": (C.c_size_t, [C.c_int, C.c_int]),
     "nyf_patch_pca": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P,
                                 C.c_size_t, _P]),

@@ -559,6 +559,53 @@ nyf_status nyf_kmeans(const float* X, int64_t N, int rho, int K, int iters, uint
   return NYF_OK;
 }
 
+nyf_status nyf_kmeans_partials(const float* X, int64_t N, int rho, int K, const float* centroids,
+                               double* sums, double* qerr, void* ws, size_t ws_bytes, void* stream) {
+  if (!X || !centroids || !sums || !qerr || N < 1 || N > ((int64_t)1 << 31) || rho < 1 ||
+      rho > NYF_MAX_RHO || K < 1 || K > NYF_MAX_K)
+    return NYF_ERR_INVALID_ARG;
+  if (kmeans_smem_bytes(K, rho) > 227 * 1024) return NYF_ERR_UNSUPPORTED;
+  WsShape s{(int)N, 1, N, 1, rho, K, N, false, false, false, false};
+  const WsLayout L = ws_layout(s);
+  if (!ws_ok(ws, ws_bytes, L.km_qpart + sizeof(float) * kKmeansBlocks)) return NYF_ERR_WORKSPACE;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = reinterpret_cast<char*>(ws);
+  DevState* state = reinterpret_cast<DevState*>(w + L.state);
+  NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
+  NYF_TRY(launch_kmeans_partials(X, N, rho, K, centroids, sums, qerr,
+                                 reinterpret_cast<float*>(w + L.km_part),
+                                 reinterpret_cast<float*>(w + L.km_qpart), state, st));
+  return NYF_OK;
+}
+
+nyf_status nyf_kmeans_apply_sums(const double* sums, int K, int rho, float* centroids, void* stream) {
+  if (!sums || !centroids || K < 1 || K > NYF_MAX_K || rho < 1 || rho > NYF_MAX_RHO)
+    return NYF_ERR_INVALID_ARG;
+  NYF_TRY(launch_apply_sums(sums, K, rho, centroids, reinterpret_cast<cudaStream_t>(stream)));
+  return NYF_OK;
+}
+
+nyf_status nyf_gather_rows(const float* X, int64_t N, int rho, int64_t row0, const int64_t* idx,
+                           int K, float* out, void* stream) {
+  if (!X || !idx || !out || N < 1 || rho < 1 || K < 1 || K > NYF_MAX_K || row0 < 0)
+    return NYF_ERR_INVALID_ARG;
+  NYF_TRY(launch_gather_rows(X, N, rho, row0, idx, K, out, reinterpret_cast<cudaStream_t>(stream)));
+  return NYF_OK;
+}
+
+int nyf_draw_indices(uint64_t seed, int64_t N, int K, int64_t* out) {
+  if (!out || N < 1 || K < 1 || K > NYF_MAX_K || K > N) return 0;
+  int cnt = 0;
+  const uint64_t max_draws = 64ull * (uint64_t)K + 4096ull;   // as the device draw
+  for (uint64_t t = 1; t <= max_draws && cnt < K; ++t) {
+    const int64_t c = (int64_t)(splitmix64(seed, t) % (uint64_t)N);
+    bool dup = false;
+    for (int q = 0; q < cnt; ++q) dup |= out[q] == c;
+    if (!dup) out[cnt++] = c;
+  }
+  return cnt;
+}
+
 nyf_status nyf_features(const float* guide, int64_t N, int rho, const float* landmarks, int K,
                         float sigma_r, double eig_rel_tol, int precision, void* phi, int* rank,
                         double* alphas, void* ws, size_t ws_bytes, void* stream) {

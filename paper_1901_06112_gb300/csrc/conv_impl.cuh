@@ -11,10 +11,12 @@
 // (written once here instead of being recomputed there).
 //
 // Zero padding outside the image is the window clipping of Eq. (1).  The taps
-// g(z) = exp(-z^2 / (2 sigma_s^2)) (or 1 for the box) come from the launch
-// parameters (constant bank); the window radius S is a compile-time bound
-// (taps with |z| above the true radius are zero) so that the register-blocked
-// FIR loops fully unroll.
+// g(z) = exp(-z^2 / (2 sigma_s^2)) come from the launch parameters (constant
+// bank); the window radius S is a compile-time bound (taps with |z| above the
+// true radius are zero) so that the register-blocked FIR loops fully unroll.
+// The box window (the NLM search window) runs as running sums over the true
+// radius instead: the first output of a row or column segment sums 2S+1 inputs,
+// each next one adds the entering input and subtracts the leaving one.
 #pragma once
 
 #include "nyf_internal.cuh"
@@ -205,19 +207,35 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
         const bool a_den = qa == n, b_den = qb == n, b_none = qb > n;
         if (vactive) {
           float2 va[RV];
-#pragma unroll
-          for (int j = 0; j < RV; ++j) va[j] = f2(0.f, 0.f);
-#pragma unroll
-          for (int i = 0; i < RV + 2 * S; ++i) {
+          auto vin = [&](int i) {     // (phi f_qa, phi f_qb) at halo row vy0 + i of column vx
             const int off = (vy0 + i) * PS + vx;
             const float p = P[off];
-            const float x = a_den ? p : p * Fa[off];
-            const float y = b_den ? p : (b_none ? 0.f : p * Fb[off]);
-            const float2 v = f2(x, y);
+            return f2(a_den ? p : p * Fa[off], b_den ? p : (b_none ? 0.f : p * Fb[off]));
+          };
+          if (a.box) {
+            // box window: running sums over the true radius (2 operations per output
+            // after the first; the halo is that of the compiled radius S)
+            const int lo = S - a.S_true, T1 = 2 * a.S_true + 1;
+            float2 run = f2(0.f, 0.f);
+            for (int i = lo; i < lo + T1; ++i) run = __ffma2_rn(f2(1.f, 1.f), vin(i), run);
+            va[0] = run;
 #pragma unroll
-            for (int j = 0; j < RV; ++j) {
-              const int t = i - j;
-              if (t >= 0 && t < T) va[j] = __ffma2_rn(g[t], v, va[j]);
+            for (int j = 1; j < RV; ++j) {
+              run = __ffma2_rn(f2(1.f, 1.f), vin(j + lo + T1 - 1), run);
+              run = __ffma2_rn(f2(-1.f, -1.f), vin(j - 1 + lo), run);
+              va[j] = run;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < RV; ++j) va[j] = f2(0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < RV + 2 * S; ++i) {
+              const float2 v = vin(i);
+#pragma unroll
+              for (int j = 0; j < RV; ++j) {
+                const int t = i - j;
+                if (t >= 0 && t < T) va[j] = __ffma2_rn(g[t], v, va[j]);
+              }
             }
           }
 #pragma unroll
@@ -225,15 +243,29 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
         }
         __syncthreads();
         float2 hb[RH];
+        if (a.box) {                             // running sums along the row
+          const float2* mr = M + hy * PS + hx0;
+          const int lo = S - a.S_true, T1 = 2 * a.S_true + 1;
+          float2 run = f2(0.f, 0.f);
+          for (int i = lo; i < lo + T1; ++i) run = __ffma2_rn(f2(1.f, 1.f), mr[i], run);
+          hb[0] = run;
 #pragma unroll
-        for (int j = 0; j < RH; ++j) hb[j] = f2(0.f, 0.f);
+          for (int j = 1; j < RH; ++j) {
+            run = __ffma2_rn(f2(1.f, 1.f), mr[j + lo + T1 - 1], run);
+            run = __ffma2_rn(f2(-1.f, -1.f), mr[j - 1 + lo], run);
+            hb[j] = run;
+          }
+        } else {
 #pragma unroll
-        for (int i = 0; i < RH + 2 * S; ++i) {
-          const float2 v = M[hy * PS + hx0 + i];
+          for (int j = 0; j < RH; ++j) hb[j] = f2(0.f, 0.f);
 #pragma unroll
-          for (int j = 0; j < RH; ++j) {
-            const int t = i - j;
-            if (t >= 0 && t < T) hb[j] = __ffma2_rn(g[t], v, hb[j]);
+          for (int i = 0; i < RH + 2 * S; ++i) {
+            const float2 v = M[hy * PS + hx0 + i];
+#pragma unroll
+            for (int j = 0; j < RH; ++j) {
+              const int t = i - j;
+              if (t >= 0 && t < T) hb[j] = __ffma2_rn(g[t], v, hb[j]);
+            }
           }
         }
 #pragma unroll

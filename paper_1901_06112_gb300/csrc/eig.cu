@@ -131,12 +131,10 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi32(int K, EigBuf* b) {
         if (i < j) off += sm.A[i][j] * sm.A[i][j];
       }
       off = block_sum_f(off, sm.red);
-      // stop once the off-diagonal norm is below ~3e-5 of the diagonal's: the three
-      // FP64 refinement iterations that follow square the error each (3e-5 -> 1e-9
-      // -> 1e-18), and clusters go to the polish; or once FP32 rounding noise stops
-      // the decrease
-      if (off <= 1e-9f * diag2 || off == 0.f) break;
-      if (off <= 1e-7f * diag2 && off > 0.25f * prev) break;
+      // stop at convergence, or once FP32 rounding noise stops the decrease
+      // (only near the noise floor: early sweeps can decrease slowly)
+      if (off <= 1e-14f * diag2 || off == 0.f) break;
+      if (off <= 1e-9f * diag2 && off > 0.25f * prev) break;
       prev = off;
       for (int step = 0; step < Kp - 1; ++step) {
         if (tid < half) {        // rotation of pair tid (Golub & Van Loan, sym.schur2)
@@ -144,11 +142,14 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi32(int K, EigBuf* b) {
           if (a > bb) { const int t = a; a = bb; bb = t; }
           float c = 1.f, s = 0.f;
           if (bb < K) {
-            const float apq = sm.A[a][bb];
-            if (apq != 0.f) {
+            const float apq = sm.A[a][bb], app = sm.A[a][a], aqq = sm.A[bb][bb];
+            // entries below FP32 resolution of the diagonal (subnormal ones included) are
+            // not rotated: 1 / (2 apq) must stay finite, since the diagonal starts equal
+            // (A_ii = 1) and 0 * inf would be NaN
+            if (fabsf(apq) > 1e-30f * (fabsf(app) + fabsf(aqq)) && fabsf(apq) > 1e-36f) {
               // fast reciprocal and square root: any (c, s) with c^2 + s^2 = 1 keeps V
               // orthogonal, and the FP64 refinement restores the accuracy
-              const float theta = (sm.A[bb][bb] - sm.A[a][a]) * __frcp_rn(2.f * apq);
+              const float theta = (aqq - app) * __frcp_rn(2.f * apq);
               const float at = fabsf(theta);
               const float t = at < 1e18f ? copysignf(__frcp_rn(at + __fsqrt_rn(fmaf(at, at, 1.f))), theta)
                                          : copysignf(0.5f * __frcp_rn(at), theta);
@@ -434,11 +435,16 @@ __global__ void k_finalize(int K, double tau, EigBuf* b, double* __restrict__ al
   const int tid = threadIdx.x;
   if (tid < K) lam[tid] = b->lam[tid];
   __syncthreads();
-  if (tid < K) {                                  // stable descending rank of each eigenvalue
-    const double v = lam[tid];
+  if (tid < K) {   // stable descending rank of each eigenvalue; NaN ranks last, so the
+                   // ranks are a permutation whatever the values (order[] indexes memory)
+    const double v = isnan(lam[tid]) ? -INFINITY : lam[tid];
     int rk = 0;
-    for (int q = 0; q < K; ++q) rk += (lam[q] > v) || (lam[q] == v && q < tid);
+    for (int q = 0; q < K; ++q) {
+      const double w = isnan(lam[q]) ? -INFINITY : lam[q];
+      rk += (w > v) || (w == v && q < tid);
+    }
     b->order[rk] = tid;
+    if (!isfinite(lam[tid])) b->bad = 1;
   }
   __syncthreads();
   if (tid == 0) {

@@ -378,6 +378,50 @@ k_update(const float* __restrict__ part, int nblk, int rho, int K, float* __rest
   if (tid < rho && sum[rho] > 0.0) cent[j * rho + tid] = (float)(sum[tid] / sum[rho]);
 }
 
+// Strip processing: the FP64 sums of the block partials without the division
+// (sums[j][d], d < rho; sums[j][rho] = the count), one CTA per cluster, in the
+// fixed order of k_update, so that partial sums of several strips can be added
+// (all-reduced) before the centroids move.
+__global__ void __launch_bounds__(256)
+k_sums(const float* __restrict__ part, int nblk, int rho, int K, double* __restrict__ sums) {
+  __shared__ double red[256];
+  const int j = blockIdx.x, tid = threadIdx.x, stride = rho + 1;
+  const int G = 256 / stride;
+  const int g = tid / stride, d = tid - g * stride;
+  double s = 0.0;
+  if (g < G) {
+    const float* src = part + (int64_t)j * stride + d;
+    const int64_t step = (int64_t)K * stride;
+    for (int b = g; b < nblk; b += G) s += (double)src[b * step];
+  }
+  red[tid] = s;
+  __syncthreads();
+  if (tid < stride) {
+    double t = 0.0;
+    for (int q = 0; q < G; ++q) t += red[q * stride + tid];
+    sums[j * stride + tid] = t;
+  }
+}
+
+// Centroid j = sums[j][0..rho) / sums[j][rho]; kept if the count is zero.
+__global__ void k_apply_sums(const double* __restrict__ sums, int K, int rho, float* __restrict__ cent) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * rho; e += gridDim.x * blockDim.x) {
+    const int j = e / rho, d = e - j * rho;
+    const double c = sums[j * (rho + 1) + rho];
+    if (c > 0.0) cent[e] = (float)(sums[j * (rho + 1) + d] / c);
+  }
+}
+
+// out[j] = row idx[j] - row0 of X (N rows) when it lies in this strip, else zeros.
+__global__ void k_gather_rows(const float* __restrict__ X, int64_t N, int rho, int64_t row0,
+                              const int64_t* __restrict__ idx, int K, float* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * rho; e += gridDim.x * blockDim.x) {
+    const int j = e / rho, d = e - j * rho;
+    const int64_t r = idx[j] - row0;
+    out[e] = (r >= 0 && r < N) ? X[r * rho + d] : 0.f;
+  }
+}
+
 // Quantisation error e = sum of the block partials (FP64, fixed order).
 __global__ void k_qerr(const float* __restrict__ qpart, int nblk, double* __restrict__ out,
                        DevState* state) {
@@ -490,6 +534,38 @@ cudaError_t launch_kmeans(const float* X, int64_t N, int rho, int K, int iters, 
   cudaError_t e = assign_dispatch(grid, X, N, rho, K, centroids, labels, part, qpart, 0, st);
   if (e != cudaSuccess) return e;
   k_qerr<<<1, 256, 0, st>>>(qpart, grid, qerr_out, state);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kmeans_partials(const float* X, int64_t N, int rho, int K, const float* cent,
+                                   double* sums, double* qerr, float* part, float* qpart,
+                                   DevState* state, cudaStream_t st) {
+  cudaError_t e;
+  int grid;
+  if (assign_tc_supported(rho, K)) {
+    grid = assign_tc_grid(N);
+    e = launch_assign_tc(grid, X, N, rho, K, cent, nullptr, part, qpart, 1, state, st);
+  } else {
+    grid = kmeans_grid(N, rho);
+    e = assign_dispatch(grid, X, N, rho, K, cent, nullptr, part, qpart, 1, st);
+  }
+  if (e != cudaSuccess) return e;
+  k_sums<<<K, 256, 0, st>>>(part, grid, rho, K, sums);
+  k_qerr<<<1, 256, 0, st>>>(qpart, grid, qerr, state);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_sums(const double* sums, int K, int rho, float* cent, cudaStream_t st) {
+  k_apply_sums<<<(K * rho + 255) / 256, 256, 0, st>>>(sums, K, rho, cent);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const float* X, int64_t N, int rho, int64_t row0, const int64_t* idx,
+                               int K, float* out, cudaStream_t st) {
+  k_gather_rows<<<(K * rho + 255) / 256, 256, 0, st>>>(X, N, rho, row0, idx, K, out);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -79,6 +79,14 @@ cudaError_t launch_kmeans(const float* X, int64_t N, int rho, int K, int iters, 
 cudaError_t launch_sample_rows(const float* guide, int64_t N, int rho, int64_t Ns, uint64_t seed,
                                int64_t* idx, float* X, cudaStream_t st);
 size_t kmeans_smem_bytes(int K, int rho);
+// Strip processing: one assignment pass's FP64 partial sums and error, the
+// centroid update from (all-reduced) sums, and the gather of drawn rows.
+cudaError_t launch_kmeans_partials(const float* X, int64_t N, int rho, int K, const float* cent,
+                                   double* sums, double* qerr, float* part, float* qpart,
+                                   DevState* state, cudaStream_t st);
+cudaError_t launch_apply_sums(const double* sums, int K, int rho, float* cent, cudaStream_t st);
+cudaError_t launch_gather_rows(const float* X, int64_t N, int rho, int64_t row0, const int64_t* idx,
+                               int K, float* out, cudaStream_t st);
 // Tensor-core (tcgen05) assignment pass for rows of dimension 16..80 (kmeans_tc.cu).
 bool assign_tc_supported(int rho, int K);
 int assign_tc_grid(int64_t N);
