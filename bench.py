@@ -94,9 +94,15 @@ def hbm_peak():
 
 
 def iir_bytes_per_pixel(K, n):
-    """Algorithmic DRAM bytes per pixel of the two recursive-Gaussian passes:
-    column pass reads phi (4 K) and f (4 n), writes the K (n + 1) planes Y;
-    row pass reads Y and phi, writes g_hat (4 n) and eta (4)."""
+    """Algorithmic DRAM bytes per pixel of the convolution + combine stage (the method's
+    own traffic): phi (4 K) and f (4 n) read, g_hat (4 n) and eta (4) written."""
+    return 4 * K + 8 * n + 4
+
+
+def iir_design_bytes_per_pixel(K, n):
+    """DRAM bytes per pixel of the two recursive-Gaussian passes as built: the column pass
+    reads phi and f and writes the K (n + 1) vertically filtered planes Y; the row pass
+    reads Y and phi and writes g_hat and eta."""
     return 4 * K + 4 * n + 4 * K * (n + 1) + 4 * K * (n + 1) + 4 * K + 4 * n + 4
 
 
@@ -592,6 +598,7 @@ def iir_extra(nyf, lib, f_dev, wl, steps, flush, stream):
     st = nyf.stats(ws)
     planes = wl.K if st["rank"] > 0 else 0
     gb = iir_bytes_per_pixel(planes, n) * H * W / 1e9
+    gb_design = iir_design_bytes_per_pixel(planes, n) * H * W / 1e9
     pk, how = hbm_peak()
     a = gb / (stages[3] / 1e3)
     return {"workload": wl.name + "_recursive_gaussian", "value": H * W / 1e6 / (ms / 1e3),
@@ -601,8 +608,11 @@ def iir_extra(nyf, lib, f_dev, wl, steps, flush, stream):
                          "achieved": a, "peak": pk, "unit": "GB/s", "frac": a / pk,
                          "traffic": NCU_TRAFFIC[("recursive_pair", "fp32")]
                          if (H, W, planes) == (1080, 1920, 32) else None,
-                         "algorithmic_GB": gb,
-                         "peak_basis": f"copy bandwidth ({how})"}}
+                         "algorithmic_GB": gb, "design_GB": gb_design,
+                         "design_frac": gb_design / (stages[3] / 1e3) / pk,
+                         "peak_basis": f"copy bandwidth ({how}); algorithmic bytes = f, phi "
+                                       "read, g_hat, eta written; design bytes add the "
+                                       "K (n+1)-plane intermediate"}}
 
 
 def pca_nlm_extra(nyf, steps, flush, stream):

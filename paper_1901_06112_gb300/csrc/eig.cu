@@ -144,16 +144,11 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi32(int K, EigBuf* b) {
           if (bb < K) {
             const float apq = sm.A[a][bb], app = sm.A[a][a], aqq = sm.A[bb][bb];
             // entries below FP32 resolution of the diagonal (subnormal ones included) are
-            // not rotated: 1 / (2 apq) must stay finite, since the diagonal starts equal
-            // (A_ii = 1) and 0 * inf would be NaN
+            // not rotated, so that theta stays finite
             if (fabsf(apq) > 1e-30f * (fabsf(app) + fabsf(aqq)) && fabsf(apq) > 1e-36f) {
-              // fast reciprocal and square root: any (c, s) with c^2 + s^2 = 1 keeps V
-              // orthogonal, and the FP64 refinement restores the accuracy
-              const float theta = (aqq - app) * __frcp_rn(2.f * apq);
-              const float at = fabsf(theta);
-              const float t = at < 1e18f ? copysignf(__frcp_rn(at + __fsqrt_rn(fmaf(at, at, 1.f))), theta)
-                                         : copysignf(0.5f * __frcp_rn(at), theta);
-              c = rsqrtf(fmaf(t, t, 1.f));
+              const float theta = (aqq - app) / (2.f * apq);
+              const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(1.f + theta * theta));
+              c = rsqrtf(1.f + t * t);
               s = t * c;
             }
           } else {
@@ -165,43 +160,13 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi32(int K, EigBuf* b) {
           sm.s[tid] = s;
         }
         __syncthreads();
-        // 2 x 2 blocks of A: rows of pair u, columns of pair v.  A thread's blocks are
-        // disjoint from every other thread's, so all of its loads are issued first and
-        // the stores follow (one shared-memory round trip per step, not one per block).
-        constexpr int kBlk = (kMaxK / 2) * (kMaxK / 2) / kJacThreads;
-        float la[kBlk][4];
-#pragma unroll
-        for (int o = 0; o < kBlk; ++o) {
-          const int e = tid + o * kJacThreads;
-          if (e < half * half) {
-            const int u = e / half, v = e - u * half;
-            const int pu = sm.p[u], qu = sm.q[u], pv = sm.p[v], qv = sm.q[v];
-            la[o][0] = sm.A[pu][pv];
-            la[o][1] = sm.A[pu][qv];
-            la[o][2] = sm.A[qu][pv];
-            la[o][3] = sm.A[qu][qv];
-          }
-        }
-        constexpr int kVt = kMaxK * (kMaxK / 2) / kJacThreads;
-        float lv[kVt][2];
-#pragma unroll
-        for (int o = 0; o < kVt; ++o) {
-          const int e = tid + o * kJacThreads;
-          if (e < K * half) {
-            const int i = e / half, v = e - i * half;
-            lv[o][0] = sm.V[i][sm.p[v]];
-            lv[o][1] = sm.V[i][sm.q[v]];
-          }
-        }
-#pragma unroll
-        for (int o = 0; o < kBlk; ++o) {
-          const int e = tid + o * kJacThreads;
-          if (e < half * half) {
+        // 2 x 2 blocks of A: rows of pair u, columns of pair v
+        for (int e = tid; e < half * half; e += kJacThreads) {
           const int u = e / half, v = e - u * half;
           const int pu = sm.p[u], qu = sm.q[u], pv = sm.p[v], qv = sm.q[v];
           const float cu = sm.c[u], su = sm.s[u], cv = sm.c[v], sv = sm.s[v];
-          const float a00 = la[o][0], a01 = la[o][1];
-          const float a10 = la[o][2], a11 = la[o][3];
+          const float a00 = sm.A[pu][pv], a01 = sm.A[pu][qv];
+          const float a10 = sm.A[qu][pv], a11 = sm.A[qu][qv];
           // rows: [r0; r1] = R_u^T [a0.; a1.]
           const float r00 = cu * a00 - su * a10, r01 = cu * a01 - su * a11;
           const float r10 = su * a00 + cu * a10, r11 = su * a01 + cu * a11;
@@ -220,20 +185,17 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi32(int K, EigBuf* b) {
             sm.A[pu][pv] = n00;
             sm.A[pu][qv] = n01;
             sm.A[qu][pv] = n10;
-            sm.A[qu][qv] = (u == v) ? n11 : n11;
+            sm.A[qu][qv] = n11;
             if (u == v) sm.A[pu][qv] = sm.A[qu][pv] = 0.f;   // the annihilated entry
           }
-          }
         }
-        // V <- V J: columns of pair v (values loaded above)
-#pragma unroll
-        for (int o = 0; o < kVt; ++o) {
-          const int e = tid + o * kJacThreads;
+        // V <- V J: columns of pair v
+        for (int e = tid; e < K * half; e += kJacThreads) {
           const int i = e / half, v = e - i * half;
-          const int pv = e < K * half ? sm.p[v] : 0, qv = e < K * half ? sm.q[v] : 0;
+          const int pv = sm.p[v], qv = sm.q[v];
           if (pv != qv) {
             const float cv = sm.c[v], sv = sm.s[v];
-            const float x = lv[o][0], y = lv[o][1];
+            const float x = sm.V[i][pv], y = sm.V[i][qv];
             sm.V[i][pv] = cv * x - sv * y;
             sm.V[i][qv] = sv * x + cv * y;
           }
