@@ -26,7 +26,7 @@ constexpr int kFbThreads = 256;
 __host__ __device__ inline int kpad4(int K) { return (K + 3) & ~3; }
 
 template <int KB, int RB>
-__global__ void __launch_bounds__(kFbThreads)
+__global__ void __launch_bounds__(kFbThreads, (KB <= 32 && RB != 32) ? 3 : 1)
 k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float* __restrict__ lm,
                int K, float inv2s2r, const float* __restrict__ what,
                const DevState* __restrict__ state, const float* __restrict__ dphi,
@@ -52,11 +52,18 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
     Wsm[e] = k < K ? what[m * K + k] : 0.f;
   }
   for (int e = tid; e < K * rho; e += blockDim.x) mu[e] = lm[e];
-  // this thread's 2 x 2 blocks of G_W = E^T dPhi
-  constexpr int kMaxOwn = (KB / 2) * (KB / 2) / kFbThreads > 0 ? (KB / 2) * (KB / 2) / kFbThreads : 1;
-  float gw[kMaxOwn][4];
+  // this thread's 4 x 4 block of G_W = E^T dPhi: block (m0, k0) = (4 (blk / rb4), 4 (blk % rb4));
+  // with fewer blocks than threads, group g of the threads takes the pixels px = g mod G
+  // of each round (G groups, combined in a fixed order at the end)
+  const int rb4 = (state->planes + 3) / 4, nb4 = (K + 3) / 4;
+  const int nblk4 = nb4 * (rb4 > 0 ? rb4 : 1);
+  const int G = kFbThreads / nblk4 > 0 ? kFbThreads / nblk4 : 1;
+  const int grp = tid / nblk4, blk = tid - grp * nblk4;
+  const bool own = grp < G && rb4 > 0;
+  const int m0 = 4 * (blk / (rb4 > 0 ? rb4 : 1)), k0 = 4 * (blk % (rb4 > 0 ? rb4 : 1));
+  float gw[16];
 #pragma unroll
-  for (int o = 0; o < kMaxOwn; ++o) gw[o][0] = gw[o][1] = gw[o][2] = gw[o][3] = 0.f;
+  for (int q = 0; q < 16; ++q) gw[q] = 0.f;
   float srp = 0.f;
   __syncthreads();
 
@@ -148,47 +155,37 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
 #pragma unroll
     for (int k = 0; k < KB; ++k) Ds[tid * KB + k] = g[k];
     __syncthreads();
-    // G_W += E^T dPhi over this round's pixels (four independent partial sums)
-    const int nb = (K + 1) / 2, rb = (r + 1) / 2;
+    // G_W += E^T dPhi over this round's pixels: two 16-byte loads per 16 FMAs
+    if (own) {
+      for (int px = grp; px < kFbThreads; px += G) {
+        const float4 ev = *reinterpret_cast<const float4*>(Es + px * KB + m0);
+        const float4 dv = *reinterpret_cast<const float4*>(Ds + px * KB + k0);
+        const float e4[4] = {ev.x, ev.y, ev.z, ev.w}, d4[4] = {dv.x, dv.y, dv.z, dv.w};
 #pragma unroll
-    for (int o = 0; o < kMaxOwn; ++o) {
-      const int blk = tid + o * kFbThreads;
-      if (blk < nb * rb) {
-        const int m0 = 2 * (blk / rb), k0 = 2 * (blk % rb);
-        float s[4][4];
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s[u][0] = s[u][1] = s[u][2] = s[u][3] = 0.f;
-        for (int px = 0; px < kFbThreads; px += 4) {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float2 ev = *reinterpret_cast<const float2*>(Es + (px + u) * KB + m0);
-            const float2 dv = *reinterpret_cast<const float2*>(Ds + (px + u) * KB + k0);
-            s[u][0] = fmaf(ev.x, dv.x, s[u][0]);
-            s[u][1] = fmaf(ev.x, dv.y, s[u][1]);
-            s[u][2] = fmaf(ev.y, dv.x, s[u][2]);
-            s[u][3] = fmaf(ev.y, dv.y, s[u][3]);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) gw[o][q] += (s[0][q] + s[1][q]) + (s[2][q] + s[3][q]);
+          for (int c = 0; c < 4; ++c) gw[a * 4 + c] = fmaf(e4[a], d4[c], gw[a * 4 + c]);
       }
     }
     __syncthreads();
   }
-  // block partials: G_W (K x K, entries k >= r stay zero) and the sigma_r term
-  const int nb = (K + 1) / 2, rb = (r + 1) / 2;
+  // block partials: G_W (K x K, entries k >= r stay zero) and the sigma_r term.  The
+  // groups' sums go through shared memory (the Es region, free now) and are added in
+  // group order.
   float* gp = gw_part + (int64_t)blockIdx.x * K * K;
   for (int e = tid; e < K * K; e += blockDim.x) gp[e] = 0.f;
-  __syncthreads();
+  float* gs = Es;   // G x nblk4 x 16 <= 16 kFbThreads floats: Es and Ds (2 KB kFbThreads), both free now
+  if (own) {
 #pragma unroll
-  for (int o = 0; o < kMaxOwn; ++o) {
-    const int blk = tid + o * kFbThreads;
-    if (blk < nb * rb) {
-      const int m0 = 2 * (blk / rb), k0 = 2 * (blk % rb);
-      if (m0 < K && k0 < r) gp[m0 * K + k0] = gw[o][0];
-      if (m0 < K && k0 + 1 < r) gp[m0 * K + k0 + 1] = gw[o][1];
-      if (m0 + 1 < K && k0 < r) gp[(m0 + 1) * K + k0] = gw[o][2];
-      if (m0 + 1 < K && k0 + 1 < r) gp[(m0 + 1) * K + k0 + 1] = gw[o][3];
+    for (int q = 0; q < 16; ++q) gs[(grp * nblk4 + blk) * 16 + q] = gw[q];
+  }
+  __syncthreads();
+  if (own && grp == 0) {
+    for (int q = 0; q < 16; ++q) {
+      float t = 0.f;
+      for (int g2 = 0; g2 < G; ++g2) t += gs[(g2 * nblk4 + blk) * 16 + q];
+      const int m = m0 + q / 4, k = k0 + q % 4;
+      if (m < K && k < r) gp[m * K + k] = t;
     }
   }
   __shared__ float red[kFbThreads / 32];
