@@ -264,10 +264,11 @@ nyf_status nyf_iir_line_params(double sigma_s, int len, float* out, int out_len)
 
 /* Mean patch, all rho eigenvalues of C (descending) and the q leading
  * eigenvectors.  Covariance accumulated in FP32 per CTA from patches shifted by
- * the channel means, reduced in FP64; eigendecomposition in FP32 on one CTA by
- * parallel cyclic Jacobi (round-robin ordering, at most 20 sweeps:
- * NYF_ERR_TIMEOUT latched in ws if it has not converged; NYF_ERR_NUMERIC for a
- * non-finite eigenvalue), then the q columns re-orthonormalised in FP64.
+ * the channel means, reduced in FP64; eigendecomposition in FP32 on one CTA:
+ * Householder tridiagonalisation, every eigenvalue by bisection on Sturm
+ * counts, the q leading eigenvectors by inverse iteration (reorthogonalised
+ * within clusters of close eigenvalues) and back-transformation, then the q
+ * columns re-orthonormalised in FP64.  Every loop has a fixed trip count.
  *   mean     rho floats (device, out)
  *   basis    rho x q floats, row-major: basis[i * q + j] = component i of
  *            eigenvector j (device, out)

@@ -192,7 +192,8 @@ __global__ void k_gram_reduce(const float* __restrict__ part, int nparts, int rh
 //      earlier vectors whose eigenvalues lie within 1e-3 ||T|| (a cluster);
 //   4. back-transformation u = Q x through the reflectors (a warp per vector).
 // Every loop has a fixed trip count.
-constexpr int kPcaSweeps = 20;
+constexpr int kBisectIters = 64;
+constexpr int kInvIters = 4;
 
 __device__ __forceinline__ float block_sum_f(float x, float* red, int tid) {
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -204,172 +205,204 @@ __device__ __forceinline__ float block_sum_f(float x, float* red, int tid) {
   return s;
 }
 
-__device__ __forceinline__ int pca_player(int pos, int step, int Kp) {
-  return pos == 0 ? 0 : 1 + (pos - 1 + step) % (Kp - 1);
+// Number of eigenvalues of the tridiagonal (d, e2 = e^2) strictly below x.
+__device__ int sturm_count(const float* d, const float* e2, int n, float x, float pivmin) {
+  int c = 0;
+  float q = 1.f;
+  for (int k = 0; k < n; ++k) {
+    q = (d[k] - x) - (k > 0 ? e2[k - 1] / q : 0.f);
+    if (fabsf(q) < pivmin) q = -pivmin;
+    c += q < 0.f;
+  }
+  return c;
 }
 
-// ---- eigendecomposition of the rho x rho covariance (rho <= 160): parallel cyclic
-// Jacobi in FP32 on one CTA.  Round-robin ("circle") ordering: at step s position
-// 0 holds index 0 and position i > 0 index 1 + (i - 1 + s) mod (Kp - 1); position
-// i meets position Kp - 1 - i, so the Kp / 2 rotations of a step act on disjoint
-// index pairs and A' = J^T A J splits into independent 2 x 2 blocks (pair u, pair
-// v) -> R_u^T [A]_uv R_v.  Each thread owns a fixed set of blocks and of V's
-// column pairs per step, loads a chunk of them before storing it (no other thread
-// touches them), and two barriers separate the steps.  Entries below FP32
-// resolution of their diagonal are not rotated.  Eigenvalues are the final
-// diagonal (descending), eigenvectors the columns of V; the q leading columns go
-// to `basis` (re-orthonormalised in FP64 afterwards).
 __global__ void __launch_bounds__(kJacobiThreads) k_eig_pca(const float* __restrict__ C, int rho, int q,
                                                             float* __restrict__ eigvals,
                                                             float* __restrict__ basis, DevState* state) {
   extern __shared__ float smj[];
   const int n = rho, rp = (rho + 3) & ~3, ld = n | 1;
-  const int Kp = (n + 1) & ~1, half = Kp / 2;
   float* A = smj;                                // n x ld
-  float* V = A + n * ld;                         // n x ld
-  float* pc = V + n * ld;                        // rotation cosines (half)
-  float* ps = pc + 80;                           // sines
-  int* pp = reinterpret_cast<int*>(ps + 80);     // pair members p <= q (q = p: none)
-  int* pq = pp + 80;
-  int* ord = pq + 80;                            // eigenvalue order, descending (n)
+  float* X = A + n * ld;                         // q columns of n (eigenvectors of T, then of C)
+  float* d = X + n * q;
+  float* e = d + n;
+  float* e2 = e + n;
+  float* beta = e2 + n;
+  float* lam = beta + n;                         // ascending
+  float* vv = lam + n;                           // reflector / work vector
+  float* pw = vv + n;                            // p, then w
+  float* ga = pw + n;                            // elimination: pivots
+  float* gu1 = ga + n;                           //   first superdiagonal
+  float* gu2 = gu1 + n;                          //   second superdiagonal
+  float* gx = gu2 + n;                           //   right-hand side / solution
   __shared__ float red[kJacobiThreads / 32];
-  const int tid = threadIdx.x;
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e - i * n;
-    A[i * ld + j] = C[(size_t)i * rp + j];
-    V[i * ld + j] = i == j ? 1.f : 0.f;
-  }
+  __shared__ float bounds[3];                    // lo, hi, ||T||
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
+  (void)state;                                   // fixed trip counts: no status to latch
+  for (int i = warp; i < n; i += nwarp)
+    for (int j = lane; j < n; j += 32) A[i * ld + j] = C[(size_t)i * rp + j];
   __syncthreads();
-  const float diag2 = block_sum_f(tid < n ? A[tid * ld + tid] * A[tid * ld + tid] : 0.f, red, tid);
-  float prev = INFINITY;
-  int sweeps = 0;
-  for (; sweeps < kPcaSweeps; ++sweeps) {
-    float off = 0.f;
-    for (int e = tid; e < n * n; e += blockDim.x) {
-      const int i = e / n, j = e - i * n;
-      if (i < j) off += A[i * ld + j] * A[i * ld + j];
-    }
-    off = block_sum_f(off, red, tid);
-    if (off <= 1e-14f * diag2 || off == 0.f) break;
-    if (off <= 1e-9f * diag2 && off > 0.25f * prev) break;   // FP32 noise floor reached
-    prev = off;
-    for (int step = 0; step < Kp - 1; ++step) {
-      if (tid < half) {
-        int a = pca_player(tid, step, Kp), b = pca_player(Kp - 1 - tid, step, Kp);
-        if (a > b) { const int t = a; a = b; b = t; }
-        float c = 1.f, sn = 0.f;
-        if (b < n) {
-          const float apq = A[a * ld + b], app = A[a * ld + a], aqq = A[b * ld + b];
-          if (fabsf(apq) > 1e-30f * (fabsf(app) + fabsf(aqq)) && fabsf(apq) > 1e-36f) {
-            const float theta = (aqq - app) / (2.f * apq);
-            const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(1.f + theta * theta));
-            c = rsqrtf(1.f + t * t);
-            sn = t * c;
-          }
-        } else {
-          b = a;                                   // odd n: the dummy partner
-        }
-        pp[tid] = a;
-        pq[tid] = b;
-        pc[tid] = c;
-        ps[tid] = sn;
+  // ---- 1. tridiagonalisation
+  for (int k = 0; k < n - 2; ++k) {
+    float ss = 0.f;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) ss += A[i * ld + k] * A[i * ld + k];
+    const float sig = sqrtf(block_sum_f(ss, red, tid));
+    const float x0 = A[(k + 1) * ld + k];
+    if (!(sig > 0.f)) {                          // column already reduced (uniform)
+      if (tid == 0) {
+        e[k] = 0.f;
+        beta[k] = 0.f;
       }
       __syncthreads();
-      // 2 x 2 blocks of A, in chunks of 4 (loads of a chunk first, then its stores)
-      for (int base = tid; base < half * half; base += 4 * kJacobiThreads) {
-        float la[4][4];
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const int e = base + o * kJacobiThreads;
-          if (e < half * half) {
-            const int u = e / half, v = e - u * half;
-            const int pu = pp[u], qu = pq[u], pv = pp[v], qv = pq[v];
-            la[o][0] = A[pu * ld + pv];
-            la[o][1] = A[pu * ld + qv];
-            la[o][2] = A[qu * ld + pv];
-            la[o][3] = A[qu * ld + qv];
+      continue;
+    }
+    const float alpha = x0 >= 0.f ? -sig : sig;
+    const float b = 1.f / (sig * (sig + fabsf(x0)));
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) vv[i] = i == k + 1 ? x0 - alpha : A[i * ld + k];
+    __syncthreads();
+    for (int i = k + 1 + warp; i < n; i += nwarp) {       // p = b B v
+      float t = 0.f;
+      for (int j = k + 1 + lane; j < n; j += 32) t = fmaf(A[i * ld + j], vv[j], t);
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) pw[i] = b * t;
+    }
+    __syncthreads();
+    float vp = 0.f;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) vp += vv[i] * pw[i];
+    const float K = 0.5f * b * block_sum_f(vp, red, tid);
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) pw[i] -= K * vv[i];   // w
+    __syncthreads();
+    for (int i = k + 1 + warp; i < n; i += nwarp)            // B -= v w^T + w v^T
+      for (int j = k + 1 + lane; j < n; j += 32)
+        A[i * ld + j] -= vv[i] * pw[j] + pw[i] * vv[j];
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) A[i * ld + k] = vv[i];   // keep the reflector
+    if (tid == 0) {
+      e[k] = alpha;
+      beta[k] = b;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) e[n - 2] = A[(n - 1) * ld + (n - 2)];
+    e[n - 1] = 0.f;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) {
+    d[i] = A[i * ld + i];
+    e2[i] = e[i] * e[i];
+  }
+  __syncthreads();
+  if (tid == 0) {                                // Gershgorin interval and ||T||
+    float lo = INFINITY, hi = -INFINITY;
+    for (int i = 0; i < n; ++i) {
+      const float rad = fabsf(e[i]) + (i > 0 ? fabsf(e[i - 1]) : 0.f);
+      lo = fminf(lo, d[i] - rad);
+      hi = fmaxf(hi, d[i] + rad);
+    }
+    bounds[0] = lo;
+    bounds[1] = hi;
+    bounds[2] = fmaxf(fabsf(lo), fabsf(hi));
+  }
+  __syncthreads();
+  const float tnorm = bounds[2];
+  const float eps = 1.1920929e-7f;
+  const float pivmin = fmaxf(1e-30f, 1e-2f * eps * eps * tnorm * tnorm);
+  // ---- 2. bisection: thread i finds the i-th smallest eigenvalue
+  for (int i = tid; i < n; i += blockDim.x) {
+    float a = bounds[0], b = bounds[1];
+    for (int it = 0; it < kBisectIters; ++it) {
+      const float mid = 0.5f * (a + b);
+      if (!(mid > a && mid < b)) break;
+      if (sturm_count(d, e2, n, mid, pivmin) <= i) a = mid;
+      else b = mid;
+      if (b - a <= 2.f * eps * fmaxf(fabsf(a), fabsf(b)) + pivmin) break;
+    }
+    lam[i] = 0.5f * (a + b);
+  }
+  __syncthreads();
+  // ---- 3. inverse iteration for the q largest, warp 0 (lane 0 solves)
+  if (warp == 0) {
+    const float tiny = eps * tnorm, ortol = 1e-3f * tnorm;
+    for (int j = 0; j < q; ++j) {
+      const float lj = lam[n - 1 - j];
+      for (int i = lane; i < n; i += 32) gx[i] = (float)((37 * (i + 1) + 11 * j) % 97) / 97.f - 0.5f;
+      __syncwarp();
+      for (int it = 0; it < kInvIters; ++it) {
+        if (lane == 0) {                         // (T - lj I) y = gx, partial pivoting
+          for (int k = 0; k < n; ++k) {
+            ga[k] = d[k] - lj;
+            gu1[k] = k < n - 1 ? e[k] : 0.f;
+            gu2[k] = 0.f;
           }
-        }
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const int e = base + o * kJacobiThreads;
-          if (e < half * half) {
-            const int u = e / half, v = e - u * half;
-            const int pu = pp[u], qu = pq[u], pv = pp[v], qv = pq[v];
-            const float cu = pc[u], su = ps[u], cv = pc[v], sv = ps[v];
-            const float r00 = cu * la[o][0] - su * la[o][2], r01 = cu * la[o][1] - su * la[o][3];
-            const float r10 = su * la[o][0] + cu * la[o][2], r11 = su * la[o][1] + cu * la[o][3];
-            const float n00 = cv * r00 - sv * r01, n01 = sv * r00 + cv * r01;
-            const float n10 = cv * r10 - sv * r11, n11 = sv * r10 + cv * r11;
-            if (pu == qu && pv == qv) {
-              A[pu * ld + pv] = n00;
-            } else if (pu == qu) {
-              A[pu * ld + pv] = n00;
-              A[pu * ld + qv] = n01;
-            } else if (pv == qv) {
-              A[pu * ld + pv] = n00;
-              A[qu * ld + pv] = n10;
+          for (int k = 0; k < n - 1; ++k) {
+            const float sub = e[k];
+            if (fabsf(ga[k]) >= fabsf(sub)) {
+              if (ga[k] == 0.f) ga[k] = tiny;
+              const float m = sub / ga[k];
+              ga[k + 1] -= m * gu1[k];
+              gx[k + 1] -= m * gx[k];
             } else {
-              A[pu * ld + pv] = n00;
-              A[qu * ld + qv] = n11;
-              if (u == v) {                        // the annihilated pair
-                A[pu * ld + qv] = 0.f;
-                A[qu * ld + pv] = 0.f;
-              } else {
-                A[pu * ld + qv] = n01;
-                A[qu * ld + pv] = n10;
-              }
+              const float m = ga[k] / sub;
+              const float uk = gu1[k];
+              const float u1n = ga[k + 1];
+              const float u2n = k + 1 < n - 1 ? gu1[k + 1] : 0.f;
+              ga[k] = sub;
+              ga[k + 1] = uk - m * u1n;
+              gu1[k] = u1n;
+              gu2[k] = u2n;
+              if (k + 1 < n - 1) gu1[k + 1] = -m * u2n;
+              const float xk = gx[k];
+              gx[k] = gx[k + 1];
+              gx[k + 1] = xk - m * gx[k + 1];
             }
           }
-        }
-      }
-      // V <- V J: column pairs, in chunks of 8
-      for (int base = tid; base < n * half; base += 8 * kJacobiThreads) {
-        float lv[8][2];
-#pragma unroll
-        for (int o = 0; o < 8; ++o) {
-          const int e = base + o * kJacobiThreads;
-          if (e < n * half) {
-            const int i = e / half, v = e - i * half;
-            lv[o][0] = V[i * ld + pp[v]];
-            lv[o][1] = V[i * ld + pq[v]];
+          for (int k = n - 1; k >= 0; --k) {
+            float s = gx[k];
+            if (k + 1 < n) s -= gu1[k] * gx[k + 1];
+            if (k + 2 < n) s -= gu2[k] * gx[k + 2];
+            gx[k] = s / (ga[k] != 0.f ? ga[k] : tiny);
           }
         }
-#pragma unroll
-        for (int o = 0; o < 8; ++o) {
-          const int e = base + o * kJacobiThreads;
-          if (e < n * half) {
-            const int i = e / half, v = e - i * half;
-            const int pv = pp[v], qv = pq[v];
-            if (pv != qv) {
-              V[i * ld + pv] = pc[v] * lv[o][0] - ps[v] * lv[o][1];
-              V[i * ld + qv] = ps[v] * lv[o][0] + pc[v] * lv[o][1];
-            }
-          }
+        __syncwarp();
+        for (int i2 = 0; i2 < j; ++i2) {         // reorthogonalise inside the cluster
+          if (!(fabsf(lam[n - 1 - i2] - lj) < ortol)) continue;
+          const float* xi = X + i2 * n;
+          float dt = 0.f;
+          for (int i = lane; i < n; i += 32) dt += xi[i] * gx[i];
+          for (int o = 16; o > 0; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
+          for (int i = lane; i < n; i += 32) gx[i] -= dt * xi[i];
+          __syncwarp();
         }
+        float nn = 0.f;
+        for (int i = lane; i < n; i += 32) nn += gx[i] * gx[i];
+        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        const float inv = nn > 0.f ? rsqrtf(nn) : 0.f;
+        for (int i = lane; i < n; i += 32) gx[i] *= inv;
+        __syncwarp();
       }
-      __syncthreads();
+      for (int i = lane; i < n; i += 32) X[j * n + i] = gx[i];
+      __syncwarp();
     }
-  }
-  if (tid == 0 && sweeps == kPcaSweeps) set_status(state, NYF_ERR_TIMEOUT);
-  // descending order of the diagonal (a permutation whatever the values: NaN last)
-  if (tid < n) {
-    const float x = A[tid * ld + tid];
-    const float v = isnan(x) ? -INFINITY : x;
-    int rk = 0;
-    for (int j = 0; j < n; ++j) {
-      const float y = A[j * ld + j];
-      const float w = isnan(y) ? -INFINITY : y;
-      rk += (w > v) || (w == v && j < tid);
-    }
-    ord[rk] = tid;
-    if (!isfinite(x)) set_status(state, NYF_ERR_NUMERIC);
   }
   __syncthreads();
-  for (int k = tid; k < rho; k += blockDim.x) eigvals[k] = A[ord[k] * ld + ord[k]];
+  // ---- 4. u_j = H_0 H_1 ... H_{n-3} x_j, a warp per vector
+  for (int j = warp; j < q; j += nwarp) {
+    float* x = X + j * n;
+    for (int k = n - 3; k >= 0; --k) {
+      const float bk = beta[k];
+      if (bk == 0.f) continue;
+      float dt = 0.f;
+      for (int i = k + 1 + lane; i < n; i += 32) dt += A[i * ld + k] * x[i];
+      for (int o = 16; o > 0; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
+      for (int i = k + 1 + lane; i < n; i += 32) x[i] -= bk * dt * A[i * ld + k];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < rho; k += blockDim.x) eigvals[k] = lam[n - 1 - k];
   for (int e3 = tid; e3 < rho * q; e3 += blockDim.x) {
     const int i = e3 / q, j = e3 % q;
-    basis[e3] = V[i * ld + ord[j]];
+    basis[e3] = X[j * n + i];
   }
 }
 
@@ -494,7 +527,7 @@ size_t pca_scratch_bytes(int n, int r) {
 
 size_t pca_jacobi_smem(int rho) {
   const int ld = rho | 1;
-  return sizeof(float) * (2 * (size_t)rho * ld + 4 * 80 + (size_t)rho);
+  return sizeof(float) * ((size_t)rho * ld + (size_t)rho * 32 + 11 * (size_t)rho);
 }
 
 cudaError_t launch_patch_pca(const float* f, int H, int W, int n, int r, int q, void* scratch,
