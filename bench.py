@@ -48,6 +48,10 @@ def parse():
                     help="omega: truncated FIR Gaussian, or the recursive Gaussian (forward, fp32)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the forward-only, BF16 and batched side measurements")
+    ap.add_argument("--workload", default="colour_hd",
+                    choices=["colour_hd", "colour_256", "hyperspectral", "nlm"],
+                    help="the timed single-image workload (default: the 1920x1080 colour BLF); "
+                         "nlm runs the forward only")
     ap.add_argument("--impl", default="nyf", choices=["nyf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -326,7 +330,7 @@ def peaks():
 
 
 def stage_counts(N, n, rho, K, T, iters, Ns, fwdbwd, conv_tensor=False, feat_tensor=None,
-                 keep_planes=True, nlm_r=0):
+                 keep_planes=True, nlm_r=0, box=False):
     """Algorithmic work of each stage of one step (the method's own counts, not the
     kernels'): {stage: (bytes, fp32 FLOP, tensor FLOP, exp)}.
 
@@ -348,7 +352,8 @@ def stage_counts(N, n, rho, K, T, iters, Ns, fwdbwd, conv_tensor=False, feat_ten
     feat_flop = (2.0 * rho * K + 2.0 * K * K) * N
     c["features"] = (N * (guide_bytes + 4.0 * K), 0.0 if feat_tensor else feat_flop,
                      feat_flop if feat_tensor else 0.0, float(N * K))
-    conv_flop = N * K * q * (2.0 * T * 2 + 2)
+    # box window by running sums: 2 passes x (one add, one subtract) per output + the combine
+    conv_flop = N * K * q * ((2.0 * 2 + 2) if box else (2.0 * T * 2 + 2))
     cbytes = 4.0 * K * q * N if (fwdbwd and keep_planes) else 0.0
     c["conv_combine"] = (N * (4.0 * n + 4.0 * K + 4.0 * n + 4.0) + cbytes,
                          0.0 if conv_tensor else conv_flop, conv_flop if conv_tensor else 0.0, 0.0)
@@ -498,7 +503,7 @@ def config_line(nyf, lib, w, golden, precision, fwdbwd, steps, flush, stream):
     planes = w.K if st["rank"] > 0 else 0
     counts = stage_counts(N, n, rho, planes, 2 * w.radius + 1, w.kmeans_iters, Ns, fwdbwd,
                           conv_tensor=precision == "bf16" and w.radius <= 16 and n <= 3,
-                          nlm_r=w.patch_radius)
+                          nlm_r=w.patch_radius, box=w.spatial == "box")
     sm = {k: v for k, v in zip(STAGES, stages[:6 if fwdbwd else 4]) if v is not None}
     line = {"workload": w.name, "mode": "fwd+bwd" if fwdbwd else "fwd", "precision": precision,
             "value": N / 1e6 / (ms / 1e3), "unit": "megapixels/s", "ms_per_step": ms,
@@ -672,9 +677,12 @@ def main():
     from paper_1901_06112_gb300 import nyf, synth
 
     lib = _lib.load()
-    wl = synth.colour_blf_hd()
+    wl = {"colour_hd": synth.colour_blf_hd, "colour_256": synth.colour_blf_small,
+          "hyperspectral": synth.hyperspectral_blf, "nlm": synth.colour_nlm}[args.workload]()
     H, W, n = wl.f.shape
-    fwdbwd = args.mode == "fwdbwd"
+    nlm = wl.patch_radius > 0
+    rho = n * (2 * wl.patch_radius + 1) ** 2 if nlm else n
+    fwdbwd = args.mode == "fwdbwd" and not nlm
     iir = args.spatial == "gaussian_iir"
     if iir and (fwdbwd or args.precision != "fp32"):
         raise SystemExit("--spatial gaussian_iir runs the forward in fp32: add --mode fwd")
@@ -682,13 +690,14 @@ def main():
     def make(precision, bwd=False):
         return nyf.Params(sigma_s=wl.sigma_s, sigma_r=wl.sigma_r, K=wl.K,
                           kmeans_iters=wl.kmeans_iters, seed=replica_seed(wl.seed, rank),
-                          precision=precision,
-                          save_for_backward=bwd, spatial=args.spatial)
+                          precision=precision, save_for_backward=bwd,
+                          spatial=args.spatial if not nlm else wl.spatial, S=wl.S,
+                          patch_radius=wl.patch_radius, sample_frac=wl.sample_frac)
 
     P = make(args.precision, fwdbwd)
     f_dev = torch.from_numpy(wl.f).to(dev)
     out = torch.empty_like(f_dev)
-    ws = nyf.make_workspace(H, W, n, n, P, dev)
+    ws = nyf.make_workspace(H, W, n, rho, P, dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
     G = torch.randn(f_dev.shape, generator=torch.Generator().manual_seed(0)).to(dev)
     grads = nyf.BackwardBuffers(f_dev)
@@ -696,7 +705,10 @@ def main():
 
     def make_step(Pp, bwd):
         def step():
-            nyf.blf(f_dev, Pp, out=out, ws=ws)
+            if nlm:
+                nyf.nlm(f_dev, Pp, out=out, ws=ws)
+            else:
+                nyf.blf(f_dev, Pp, out=out, ws=ws)
             if bwd:
                 nyf.blf_backward(f_dev, Pp, out, G, ws, grads)
         return step
@@ -757,24 +769,34 @@ def main():
                     "traffic": NCU_TRAFFIC[("recursive_pair", "fp32")] if captured else None,
                     "launch_ms": stage_mean[3], "algorithmic_GB": gb,
                     "peak_basis": f"copy bandwidth ({how_h})"}
+    if wl.spatial == "box" and not iir:   # running sums: the stage is bound by its HBM bytes
+        gb = (4.0 * n + 4.0 * planes + 4.0 * n + 4.0) * H * W / 1e9
+        pk_h, how_h = hbm_peak()
+        a_h = gb / (stage_mean[3] / 1e3)
+        roof_fwd = {"kernel": "conv_combine (box window, running sums)", "bound": "hbm",
+                    "achieved": a_h, "peak": pk_h, "unit": "GB/s", "frac": a_h / pk_h,
+                    "traffic": None, "launch_ms": stage_mean[3], "algorithmic_GB": gb,
+                    "peak_basis": f"copy bandwidth ({how_h}); f and phi read, g_hat and eta written"}
     roof_bwd = roof("conv_bwd", bwd_flops, stage_mean[4]) if fwdbwd else None
     dominant = roof_bwd if (fwdbwd and stage_mean[4] > stage_mean[3]) else roof_fwd
     # Sec. 8(d) step roofline of the headline step
-    counts = stage_counts(H * W, n, n, planes, 2 * P.radius + 1, wl.kmeans_iters, H * W, fwdbwd,
-                          conv_tensor=args.precision == "bf16" and P.radius <= 16)
-    step_roof = step_roofline(counts, {k: v for k, v in zip(STAGES, stage_mean[:6])
+    counts = stage_counts(H * W, n, rho, planes, 2 * P.radius + 1, wl.kmeans_iters,
+                          max(1, int(np.floor(wl.sample_frac * H * W + 0.5))), fwdbwd,
+                          conv_tensor=args.precision == "bf16" and P.radius <= 16 and n <= 3,
+                          nlm_r=wl.patch_radius, box=wl.spatial == "box")
+    step_roof = step_roofline(counts, {k: v for k, v in zip(STAGES, stage_mean[:6 if fwdbwd else 4])
                                        if v is not None}, ms)
     accuracy = None
     if rank == 0 and not iir:
         try:
-            blocks, errs = golden_landmarks("colour_hd")
+            blocks, errs = golden_landmarks(args.workload)
             accuracy = accuracy_blf(nyf, wl, blocks[0], args.precision, fwdbwd)
             accuracy["kmeans_qerr_rel"] = abs(st["qerr"] - errs[0]) / errs[0]
         except Exception as ex:           # the accuracy pass must not hide the measurement
             accuracy = {"error": str(ex)[:300]}
 
     extras = {}
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and rank == 0 and args.workload == "colour_hd":
         lib.nyf_set_timing(0)
         if fwdbwd:                                # forward only: no planes kept
             fwd_ms, _ = timed_steps(make_step(make(args.precision), False), max(3, args.steps // 2),
@@ -879,7 +901,7 @@ def main():
                        "mode": "fwd+bwd" if fwdbwd else "fwd", "rank_r": r,
                        "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{world}"},
-            "stages_ms": dict(zip(STAGES, stage_mean[:6])),
+            "stages_ms": dict(zip(STAGES, stage_mean[:6 if fwdbwd else 4])),
             "accuracy": accuracy,
             "roofline": dominant,
             "roofline_step": step_roof,
@@ -889,7 +911,7 @@ def main():
             "clocks": clk,
             "extras": extras,
         }
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline and world == 1 and args.workload == "colour_hd":
             try:
                 line["cpu_baseline"] = cpu_baseline_obj(backward=fwdbwd)
             except Exception as ex:  # the oracle leg must not hide the GPU number
