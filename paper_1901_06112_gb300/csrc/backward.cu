@@ -55,12 +55,13 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
   // this thread's 4 x 4 block of G_W = E^T dPhi: block (m0, k0) = (4 (blk / rb4), 4 (blk % rb4));
   // with fewer blocks than threads, group g of the threads takes the pixels px = g mod G
   // of each round (G groups, combined in a fixed order at the end)
-  const int rb4 = (state->planes + 3) / 4, nb4 = (K + 3) / 4;
-  const int nblk4 = nb4 * (rb4 > 0 ? rb4 : 1);
-  const int G = kFbThreads / nblk4 > 0 ? kFbThreads / nblk4 : 1;
+  // (the block grid is that of KB, so the pixel stride G is a compile-time constant;
+  // rows of Es beyond K and of Ds beyond the kept modes are zero)
+  constexpr int nb4 = KB / 4, nblk4 = nb4 * nb4;
+  constexpr int G = kFbThreads / nblk4 > 0 ? kFbThreads / nblk4 : 1;
   const int grp = tid / nblk4, blk = tid - grp * nblk4;
-  const bool own = grp < G && rb4 > 0;
-  const int m0 = 4 * (blk / (rb4 > 0 ? rb4 : 1)), k0 = 4 * (blk % (rb4 > 0 ? rb4 : 1));
+  const bool own = grp < G;
+  const int m0 = 4 * (blk / nb4), k0 = 4 * (blk % nb4);
   float gw[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) gw[q] = 0.f;
@@ -157,6 +158,7 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
     __syncthreads();
     // G_W += E^T dPhi over this round's pixels: two 16-byte loads per 16 FMAs
     if (own) {
+#pragma unroll 4
       for (int px = grp; px < kFbThreads; px += G) {
         const float4 ev = *reinterpret_cast<const float4*>(Es + px * KB + m0);
         const float4 dv = *reinterpret_cast<const float4*>(Ds + px * KB + k0);
