@@ -414,24 +414,26 @@ cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spat
   a.adj = adj;
   a.cbuf = cbuf;
   a.box = spatial == NYF_BOX ? 1 : 0;
+  // taps of the window and their sigma_s derivative, g'(t) = g(t) t^2 / sigma_s^3, for
+  // t >= 0 (both even in t), zero beyond the true radius (the compiled radius Sc may be larger)
+  for (int t = 0; t <= kMaxTapRadius; ++t) {
+    float g = 0.f, gd = 0.f;
+    if (t <= S) {
+      if (a.box) {
+        g = 1.f;
+      } else {
+        const double s = (double)sigma_s, e = exp(-(double)t * t / (2.0 * s * s));
+        g = (float)e;
+        gd = (float)(e * t * t / (s * s * s));
+      }
+    }
+    a.tg[t] = make_float2(g, g);
+    a.td[t] = make_float2(gd, gd);
+    a.taps[kMaxTapRadius + t] = a.taps[kMaxTapRadius - t] = make_float2(g, gd);
+  }
   a.inv2s2 = a.box ? 0.f : (float)(1.0 / (2.0 * (double)sigma_s * sigma_s));
   a.inv_s3 = a.box ? 0.f : (float)(1.0 / ((double)sigma_s * sigma_s * sigma_s));
   a.S_true = S;
-  // taps of the window and their sigma_s derivative, g'(z) = g(z) z^2 / sigma_s^3,
-  // zero beyond the true radius (the compiled radius Sc may be larger)
-  for (int z = -kMaxTapRadius; z <= kMaxTapRadius; ++z) {
-    float2 t = make_float2(0.f, 0.f);
-    if (z >= -S && z <= S) {
-      if (a.box) {
-        t.x = 1.f;
-      } else {
-        const double s = (double)sigma_s, g = exp(-(double)z * z / (2.0 * s * s));
-        t.x = (float)g;
-        t.y = (float)(g * z * z / (s * s * s));
-      }
-    }
-    a.taps[kMaxTapRadius + z] = t;
-  }
   a.k_begin = k_begin;
   a.k_end = k_end;
   a.accumulate = first ? 0 : 1;

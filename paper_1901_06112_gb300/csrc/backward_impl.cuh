@@ -16,13 +16,21 @@
 // saves C_kq, so the backward convolves only u_kq, with g and g' together:
 // vertical pass (g, g') on u, horizontal pass B = g * Mb, B' = g' * Mb + g * Mb'.
 //
+// Both taps are even functions of t and g'(0) = 0, so every pass adds the two
+// inputs at +t and -t first and multiplies the sum by g(t) and by g'(t): per
+// tap pair one addition and two multiply-adds instead of four multiply-adds.
+// The quantities are handled in pairs (q, q+1) stored interleaved in shared
+// memory, so that each of those operations is one packed FP32x2 instruction
+// for two planes.
+//
 // One CTA per output tile holds all quantities of its pixels (up to four), so
 // dL/dphi_k leaves the CTA as one plane per mode without atomics.  Per mode k
-// the CTA stages phi_k once, runs the vertical pass of every quantity in one
-// balanced task list, then streams phi_{k+1} in while the horizontal pass and
-// the epilogue run.  Lanes of a warp own consecutive rows in the horizontal
-// pass (conflict-free shared-memory reads), warps own column segments.  The
-// taps come from the launch parameters (constant bank) instead of registers.
+// the CTA stages phi_k once, runs the vertical pass of every quantity pair in
+// one balanced task list, then streams phi_{k+1} in while the horizontal pass
+// and the epilogue run.  Lanes of a warp own consecutive rows in the
+// horizontal pass (conflict-free shared-memory reads), warps own column
+// segments.  The taps come from the launch parameters (constant bank) instead
+// of registers.
 #pragma once
 
 #include "conv_impl.cuh"
@@ -40,15 +48,17 @@ struct BwdArgs {
   const float* cbuf;      // planes C_kq, saved or recomputed: plane (k - k_begin) (n + 1) + q
   int k_begin, k_end;     // modes processed by this launch (k_end capped at the kept planes)
   int accumulate;         // add into df and sig_part (a later chunk of modes) instead of writing
-  float inv2s2;           // 1 / (2 sigma_s^2)
-  float inv_s3;           // 1 / sigma_s^3
-  int S_true;
   int box;
   float* dphi;            // r planes of N
   int atomic_dphi;        // quantities split over several CTAs: accumulate dphi atomically
   float* df;              // N x n, direct image term
   float* sig_part;        // one sigma_s partial per CTA
-  float2 taps[2 * kMaxTapRadius + 1];   // (g(z), g'(z)) for z = -S_compiled..S_compiled, zero beyond S
+  float inv2s2, inv_s3;
+  int S_true;
+  float2 taps[2 * kMaxTapRadius + 1];
+  // (g(t), g(t)) and (g'(t), g'(t)) for t = 0..S_compiled, zero beyond the true radius
+  float2 tg[kMaxTapRadius + 1];
+  float2 td[kMaxTapRadius + 1];
 };
 
 constexpr int kBwdThreads = 256;    // 8 warps; the taps live in the launch parameters (constant bank)
@@ -57,19 +67,23 @@ template <int S>
 struct BwdCfg {
   static constexpr int TH = 32;                                 // = lanes: one row per lane
   static constexpr int TW = S <= 16 ? 64 : (S <= 24 ? 48 : 32);
-  static constexpr int RV = 16;
+  static constexpr int RV = 8;                                  // rows per vertical task
   static constexpr int NQ = S <= 16 ? 4 : 2;                    // quantities per CTA
+  static constexpr int NP = NQ / 2;                             // quantity pairs
   static constexpr int RH = TW / (kBwdThreads / 32);            // columns per thread
   static constexpr int HH = TH + 2 * S;
   static constexpr int HW = TW + 2 * S;
-  static constexpr int PS = HW | 1;
+  static constexpr int PS = HW | 1;     // odd row stride (in elements): conflict-free walks
   static constexpr int PLANE = HH * PS;
   static constexpr int VB = TH / RV;                            // vertical row blocks
-  static constexpr int VT = NQ * VB * HW;                       // vertical tasks
+  static constexpr int VT = NP * VB * HW;                       // vertical tasks
+  // shared memory: NP interleaved adjoint pairs, phi_k, and the vertical
+  // outputs (Mb, Mb') as NP interleaved pairs each
   static constexpr size_t smem =
-      sizeof(float) * ((size_t)(NQ + 1) * PLANE + (size_t)2 * NQ * TH * PS);
+      sizeof(float) * ((size_t)2 * NP * PLANE + (size_t)PLANE + (size_t)4 * NP * TH * PS);
   static_assert(TH == 32 && RH * (kBwdThreads / 32) == TW, "lane = row, warp = segment");
-  static_assert(((NQ + 1) * PLANE) % 2 == 0, "float2 alignment of the vertical planes");
+  static_assert(NQ % 2 == 0 && TH % RV == 0, "quantity pairs, whole row blocks");
+  static_assert(PLANE % 2 == 0, "float2 alignment of the planes after phi");
   static_assert(smem <= 227 * 1024, "shared memory budget");
 };
 
@@ -98,40 +112,58 @@ __device__ __forceinline__ void bwd_stage_phi(const BwdArgs& a, float* P, int k,
   }
 }
 
+// R consecutive outputs of a symmetric FIR on a plane pair: og[j] += sum over t of
+// g(t) (x[j + S - t] + x[j + S + t]) and, with WITH_D, od[j] += the same with g'(t),
+// from inputs x[0 .. R + 2S).  The tap loop is outermost so that the 2R
+// accumulator chains interleave.
+template <int S, int R, bool WITH_D>
+__device__ __forceinline__ void sym_fir(const float2* x, const float2* tg, const float2* td,
+                                        float2 (&og)[R], float2 (&od)[R]) {
+#pragma unroll
+  for (int j = 0; j < R; ++j) og[j] = __ffma2_rn(tg[0], x[j + S], og[j]);
+#pragma unroll
+  for (int t = 1; t <= S; ++t) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const float2 s = __fadd2_rn(x[j + S - t], x[j + S + t]);
+      og[j] = __ffma2_rn(tg[t], s, og[j]);
+      if (WITH_D) od[j] = __ffma2_rn(td[t], s, od[j]);
+    }
+  }
+}
+
 template <int S>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_constant__ BwdArgs a) {
   using C = BwdCfg<S>;
-  constexpr int T = 2 * S + 1;
-  constexpr int TH = C::TH, TW = C::TW, RV = C::RV, RH = C::RH, NQ = C::NQ;
+  constexpr int TH = C::TH, RV = C::RV, RH = C::RH, NQ = C::NQ, NP = C::NP;
   constexpr int HH = C::HH, HW = C::HW, PS = C::PS, PLANE = C::PLANE;
+  constexpr bool kEarlyC = S > 16;
   extern __shared__ float sm[];
-  float* Aq = sm;                                              // NQ adjoint planes
-  float* P = Aq + NQ * PLANE;                                  // phi_k
-  float2* M = reinterpret_cast<float2*>(P + PLANE);            // NQ x TH x PS: (g, g') on u
+  float2* A2 = reinterpret_cast<float2*>(sm);                  // NP pairs (a_q, a_q+1)
+  float* P = sm + 2 * NP * PLANE;                              // phi_k
+  float2* Mg = reinterpret_cast<float2*>(P + PLANE);           // NP x TH x PS: g on u (pairs)
+  float2* Md = Mg + NP * TH * PS;                              // NP x TH x PS: g' on u (pairs)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+  const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * C::TW;
   const int q0 = blockIdx.z * NQ;
   const int n = a.n;
   const int nq = min(NQ, n + 1 - q0);                          // quantities of this CTA
   const int kb = a.k_begin;
   const int r = min(a.k_end, a.state->planes);                 // modes kb <= k < r
 
-  // adjoint planes a_q on the tile + halo (zero outside the image), then phi_0
+  // adjoint planes a_q on the tile + halo (zero outside the image and for
+  // quantities beyond n), interleaved by pairs, then phi_kb
   for (int e = tid; e < NQ * HH * HW; e += kBwdThreads) {
     const int qi = e / (HH * HW);
     const int rem = e - qi * (HH * HW);
     const int yy = rem / HW, xx = rem - yy * HW;
     const int gy = ty0 - S + yy, gx = tx0 - S + xx;
     const bool in = qi < nq && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
-    cp_async4(Aq + qi * PLANE + yy * PS + xx,
-              in ? a.adj + (int64_t)(q0 + qi) * a.N + (int64_t)gy * a.W + gx : a.adj, in);
+    float* dst = reinterpret_cast<float*>(A2 + (qi >> 1) * PLANE + yy * PS + xx) + (qi & 1);
+    cp_async4(dst, in ? a.adj + (int64_t)(q0 + qi) * a.N + (int64_t)gy * a.W + gx : a.adj, in);
   }
   if (kb < r) bwd_stage_phi<S>(a, P, kb, ty0, tx0);
   cp_async_commit();
-
-  // (g, g') tap pairs from the launch parameters: one packed FMA updates the g
-  // and g' sums of an input
-  const float2* gg = a.taps + (kMaxTapRadius - S);
 
   const int hy = lane, hx0 = warp * RH;
   const int y = ty0 + hy;
@@ -154,39 +186,70 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_consta
 
   for (int k = kb; k < r; ++k) {
     cp_async_wait<0>();
-    __syncthreads();                 // phi_k (and the adjoint planes) landed; M is free
+    __syncthreads();                 // phi_k (and the adjoint planes) landed; Mg, Md are free
     float pc[RH];                    // phi_k at this thread's pixels
 #pragma unroll
     for (int j = 0; j < RH; ++j) pc[j] = P[(hy + S) * PS + hx0 + j + S];
 
-    // vertical pass of every quantity: (g, g') on u = a_q phi_k
+    // C_kq of quantity qi at this thread's pixels, saved by the forward pass.  The
+    // loads are issued well before their use so that their latency hides under a
+    // pass: for S <= 16 before the horizontal pass of the pair, for larger radii
+    // (fewer quantities per CTA) before the vertical pass.
+    float cq[NQ][RH];
+    auto load_c = [&](int qi, float (&c)[RH]) {
+      const float* Cp =
+          a.cbuf + ((int64_t)(k - kb) * (n + 1) + q0 + qi) * a.N + (int64_t)y * a.W + tx0 + hx0;
+      const bool have = qi < nq;
+      if (RH % 4 == 0 && have && yin && tx0 + hx0 + RH <= a.W &&
+          (reinterpret_cast<uintptr_t>(Cp) & 15) == 0) {
+#pragma unroll
+        for (int m4 = 0; m4 < RH / 4; ++m4) {
+          const float4 v = __ldcs(reinterpret_cast<const float4*>(Cp) + m4);
+          c[4 * m4] = v.x;
+          c[4 * m4 + 1] = v.y;
+          c[4 * m4 + 2] = v.z;
+          c[4 * m4 + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < RH; ++j) c[j] = (have && yin && tx0 + hx0 + j < a.W) ? __ldcs(Cp + j) : 0.f;
+      }
+    };
+    if (kEarlyC) {
+#pragma unroll
+      for (int qi = 0; qi < NQ; ++qi) load_c(qi, cq[qi]);
+    }
+
+    // vertical pass of every quantity pair: (g, g') on u = a_q phi_k, RV rows of one column
     for (int task = tid; task < C::VT; task += kBwdThreads) {
-      const int qi = task / (C::VB * HW);
-      const int rem = task - qi * (C::VB * HW);
+      const int qp = task / (C::VB * HW);
+      const int rem = task - qp * (C::VB * HW);
       const int vb = rem / HW, vx = rem - vb * HW;
       const int vy0 = vb * RV;
-      if (qi < nq) {
-        const float* A = Aq + qi * PLANE;
-        float2 vm[RV];
-#pragma unroll
-        for (int j = 0; j < RV; ++j) vm[j] = make_float2(0.f, 0.f);
+      if (2 * qp < nq) {
+        const float2* Aq = A2 + qp * PLANE;
+        float2 u[RV + 2 * S];
 #pragma unroll
         for (int i = 0; i < RV + 2 * S; ++i) {
           const int off = (vy0 + i) * PS + vx;
-          const float u = P[off] * A[off];
-          const float2 uu = make_float2(u, u);
-#pragma unroll
-          for (int j = 0; j < RV; ++j) {
-            const int t = i - j;
-            if (t >= 0 && t < T) vm[j] = __ffma2_rn(gg[t], uu, vm[j]);
-          }
+          const float p = P[off];
+          const float2 av = Aq[off];
+          u[i] = make_float2(p * av.x, p * av.y);
         }
-        float2* Mq = M + qi * (TH * PS);
+        float2* mg = Mg + qp * (TH * PS) + vy0 * PS + vx;
+        float2* md = Md + qp * (TH * PS) + vy0 * PS + vx;
+        float2 og[RV], od[RV];
 #pragma unroll
-        for (int j = 0; j < RV; ++j) Mq[(vy0 + j) * PS + vx] = vm[j];
+        for (int j = 0; j < RV; ++j) og[j] = od[j] = make_float2(0.f, 0.f);
+        sym_fir<S, RV, true>(u, a.tg, a.td, og, od);
+#pragma unroll
+        for (int j = 0; j < RV; ++j) {
+          mg[j * PS] = og[j];
+          md[j * PS] = od[j];
+        }
       }
     }
-    __syncthreads();                 // M complete; nobody reads P beyond this point
+    __syncthreads();                 // Mg, Md complete; nobody reads P beyond this point
     if (k + 1 < r) {                 // phi_{k+1} streams in under the horizontal pass
       bwd_stage_phi<S>(a, P, k + 1, ty0, tx0);
       cp_async_commit();
@@ -196,49 +259,45 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_consta
 #pragma unroll
     for (int j = 0; j < RH; ++j) dacc[j] = 0.f;
 #pragma unroll
-    for (int qi = 0; qi < NQ; ++qi) {
-      if (qi < nq) {                 // uniform over the block
-        const int q = q0 + qi;
-        // C_kq at this thread's pixels, saved by the forward pass
-        const float* Cp = a.cbuf + ((int64_t)(k - kb) * (n + 1) + q) * a.N + (int64_t)y * a.W + tx0 + hx0;
-        float cq[RH];
-        if (RH % 4 == 0 && yin && tx0 + hx0 + RH <= a.W &&
-            (reinterpret_cast<uintptr_t>(Cp) & 15) == 0) {
-#pragma unroll
-          for (int m = 0; m < RH / 4; ++m) {
-            const float4 v = __ldcs(reinterpret_cast<const float4*>(Cp) + m);
-            cq[4 * m] = v.x;
-            cq[4 * m + 1] = v.y;
-            cq[4 * m + 2] = v.z;
-            cq[4 * m + 3] = v.w;
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < RH; ++j) cq[j] = (yin && tx0 + hx0 + j < a.W) ? __ldcs(Cp + j) : 0.f;
+    for (int qp = 0; qp < NP; ++qp) {
+      if (2 * qp < nq) {             // uniform over the block
+        if (!kEarlyC) {
+          load_c(2 * qp, cq[2 * qp]);
+          load_c(2 * qp + 1, cq[2 * qp + 1]);
         }
-        const float2* Mq = M + qi * (TH * PS) + hy * PS + hx0;
-        float2 bp[RH];               // (B, B') at this thread's pixels
+        // (B, B') of the pair at this thread's pixels: B = g * Mg, B' = g' * Mg + g * Md
+        float2 bg[RH], bd[RH];
+        {
+          const float2* row = Mg + qp * (TH * PS) + hy * PS + hx0;
+          float2 m[RH + 2 * S];
 #pragma unroll
-        for (int j = 0; j < RH; ++j) bp[j] = make_float2(0.f, 0.f);
+          for (int i = 0; i < RH + 2 * S; ++i) m[i] = row[i];
 #pragma unroll
-        for (int i = 0; i < RH + 2 * S; ++i) {
-          const float2 m = Mq[i];
-          const float2 mm = make_float2(m.x, m.x);
+          for (int j = 0; j < RH; ++j) bg[j] = bd[j] = make_float2(0.f, 0.f);
+          sym_fir<S, RH, true>(m, a.tg, a.td, bg, bd);
+        }
+        {
+          const float2* row = Md + qp * (TH * PS) + hy * PS + hx0;
+          float2 m[RH + 2 * S];
 #pragma unroll
-          for (int j = 0; j < RH; ++j) {
-            const int t = i - j;
-            if (t >= 0 && t < T) {
-              bp[j] = __ffma2_rn(gg[t], mm, bp[j]);        // (g Mb, g' Mb)
-              bp[j].y = fmaf(gg[t].x, m.y, bp[j].y);        //  + g Mb'
+          for (int i = 0; i < RH + 2 * S; ++i) m[i] = row[i];
+          sym_fir<S, RH, false>(m, a.tg, a.td, bd, bg);   // bg is not touched
+        }
+        const float2* Ac = A2 + qp * PLANE + (hy + S) * PS + hx0 + S;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int qi = 2 * qp + h;
+          if (qi < nq) {             // uniform over the block
+#pragma unroll
+            for (int j = 0; j < RH; ++j) {
+              const float b = h ? bg[j].y : bg[j].x;
+              const float bp = h ? bd[j].y : bd[j].x;
+              const float aq = h ? Ac[j].y : Ac[j].x;
+              dacc[j] = fmaf(aq, cq[qi][j], fmaf(fc[qi][j], b, dacc[j]));
+              dfa[qi][j] = fmaf(pc[j], b, dfa[qi][j]);
+              sig = fmaf(pc[j] * fc[qi][j], bp, sig);
             }
           }
-        }
-        const float* Ac = Aq + qi * PLANE + (hy + S) * PS + hx0 + S;
-#pragma unroll
-        for (int j = 0; j < RH; ++j) {
-          dacc[j] = fmaf(Ac[j], cq[j], fmaf(fc[qi][j], bp[j].x, dacc[j]));
-          dfa[qi][j] = fmaf(pc[j], bp[j].x, dfa[qi][j]);
-          sig = fmaf(pc[j] * fc[qi][j], bp[j].y, sig);
         }
       }
     }
