@@ -234,9 +234,24 @@ nyf_status stage_landmarks(const float* X_full, int64_t N, int rho, const nyf_pa
 
 namespace {
 
-nyf_status blf_impl(const float* f, const float* guide, int H, int W, int n, int rho,
-                    const nyf_params* p, const float* landmarks, float* out, void* ws,
-                    size_t ws_bytes, void* stream, bool timed, const int* pre_status = nullptr) {
+// Forward of one image in parts, so that the batched path can run the
+// landmark and eigendecomposition steps of all its images in shared launches:
+// fwd_prepare (checks, no launch), fwd_reset, the landmarks (stage_landmarks),
+// launch_eig, then fwd_finish (features and the convolutions + combine).
+struct FwdCtx {
+  const float* f;
+  const float* guide;
+  int H, W, n, rho;
+  const nyf_params* p;
+  float* out;
+  char* w;
+  WsLayout L;
+  DevState* state;
+  int64_t N;
+};
+
+nyf_status fwd_prepare(const float* f, const float* guide, int H, int W, int n, int rho,
+                       const nyf_params* p, float* out, void* ws, size_t ws_bytes, FwdCtx* c) {
   if (!p || p->patch_radius != 0) return NYF_ERR_INVALID_ARG;
   if (!guide) {
     if (rho != n) return NYF_ERR_INVALID_ARG;
@@ -245,41 +260,68 @@ nyf_status blf_impl(const float* f, const float* guide, int H, int W, int n, int
   nyf_status s = check_filter(f, H, W, n, rho, p, out);
   if (s != NYF_OK) return s;
   if (!aligned4(guide)) return NYF_ERR_INVALID_ARG;
-  const WsLayout L = ws_layout(shape_for(H, W, n, rho, p));
-  if (!ws_ok(ws, ws_bytes, L.total)) return NYF_ERR_WORKSPACE;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  char* w = reinterpret_cast<char*>(ws);
-  DevState* state = reinterpret_cast<DevState*>(w + L.state);
-  const int64_t N = (int64_t)H * W;
-  const int tile = resolve_tile(p);
-  NYF_TRY(cudaMemsetAsync(state, 0, sizeof(DevState), st));
+  c->L = ws_layout(shape_for(H, W, n, rho, p));
+  if (!ws_ok(ws, ws_bytes, c->L.total)) return NYF_ERR_WORKSPACE;
+  c->f = f;
+  c->guide = guide;
+  c->H = H;
+  c->W = W;
+  c->n = n;
+  c->rho = rho;
+  c->p = p;
+  c->out = out;
+  c->w = reinterpret_cast<char*>(ws);
+  c->state = reinterpret_cast<DevState*>(c->w + c->L.state);
+  c->N = (int64_t)H * W;
+  return NYF_OK;
+}
+
+nyf_status fwd_reset(const FwdCtx& c, const int* pre_status, cudaStream_t st) {
+  NYF_TRY(cudaMemsetAsync(c.state, 0, sizeof(DevState), st));
   if (pre_status)   // status of work done for this call before the filter (PCA guide)
-    NYF_TRY(cudaMemcpyAsync(&state->status, pre_status, sizeof(int), cudaMemcpyDeviceToDevice, st));
-  if (timed) timing_begin(0, 3);
-  {
-    Stage t(st, 0, timed);
-    s = stage_landmarks(guide, N, rho, p, landmarks, w, L, false, f, H, W, n, st);
-  }
-  if (s != NYF_OK) return s;
-  const float* lm = reinterpret_cast<const float*>(w + L.landmarks);
-  float* what = reinterpret_cast<float*>(w + L.what);
-  void* phi = w + L.phi;
-  {
-    Stage t(st, 1, timed);
-    NYF_TRY(launch_eig(lm, p->K, rho, p->sigma_r, p->eig_rel_tol, what, nullptr, nullptr, state,
-                       w + L.eig, st));
-  }
+    NYF_TRY(cudaMemcpyAsync(&c.state->status, pre_status, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  return NYF_OK;
+}
+
+nyf_status fwd_finish(const FwdCtx& c, cudaStream_t st, bool timed) {
+  const nyf_params* p = c.p;
+  const float* lm = reinterpret_cast<const float*>(c.w + c.L.landmarks);
+  const float* what = reinterpret_cast<const float*>(c.w + c.L.what);
+  void* phi = c.w + c.L.phi;
   {
     Stage t(st, 2, timed);
-    NYF_TRY(launch_features(guide, N, rho, lm, p->K, p->sigma_r, what, state, phi, false, st));
+    NYF_TRY(launch_features(c.guide, c.N, c.rho, lm, p->K, p->sigma_r, what, c.state, phi, false, st));
   }
   {
     Stage t(st, 3, timed);
-    NYF_TRY(spatial_combine(f, H, W, n, p, tile, w, L, out,
+    NYF_TRY(spatial_combine(c.f, c.H, c.W, c.n, p, resolve_tile(p), c.w, c.L, c.out,
                             p->save_for_backward == NYF_SAVE_PLANES
-                                ? reinterpret_cast<float*>(w + L.cbuf) : nullptr, st));
+                                ? reinterpret_cast<float*>(c.w + c.L.cbuf) : nullptr, st));
   }
   return NYF_OK;
+}
+
+nyf_status blf_impl(const float* f, const float* guide, int H, int W, int n, int rho,
+                    const nyf_params* p, const float* landmarks, float* out, void* ws,
+                    size_t ws_bytes, void* stream, bool timed, const int* pre_status = nullptr) {
+  FwdCtx c;
+  nyf_status s = fwd_prepare(f, guide, H, W, n, rho, p, out, ws, ws_bytes, &c);
+  if (s != NYF_OK) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if ((s = fwd_reset(c, pre_status, st)) != NYF_OK) return s;
+  if (timed) timing_begin(0, 3);
+  {
+    Stage t(st, 0, timed);
+    s = stage_landmarks(c.guide, c.N, rho, p, landmarks, c.w, c.L, false, f, H, W, n, st);
+  }
+  if (s != NYF_OK) return s;
+  {
+    Stage t(st, 1, timed);
+    NYF_TRY(launch_eig(reinterpret_cast<const float*>(c.w + c.L.landmarks), p->K, rho, p->sigma_r,
+                       p->eig_rel_tol, reinterpret_cast<float*>(c.w + c.L.what), nullptr, nullptr,
+                       c.state, c.w + c.L.eig, st));
+  }
+  return fwd_finish(c, st, timed);
 }
 
 nyf_status blf_backward_impl(const float* f, const float* guide, int H, int W, int n, int rho,
@@ -407,9 +449,11 @@ void assign_streams(const nyf_batch_item* items, int B, int* stream_of) {
   }
 }
 
-template <typename Fn>
+// pre(offs, total, caller): work on the caller's stream before the fork (the
+// stage-batched steps); per_image(b, params, ws, bytes, stream): image b on its pool stream.
+template <typename Pre, typename Fn>
 nyf_status run_batched(const nyf_batch_item* items, int B, int n, const nyf_params* p, void* ws,
-                       size_t ws_bytes, void* stream, Fn&& per_image) {
+                       size_t ws_bytes, void* stream, Pre&& pre, Fn&& per_image) {
   if (!items || B < 1 || !p) return NYF_ERR_INVALID_ARG;
   std::vector<size_t> offs(B);
   size_t total = 0;
@@ -419,15 +463,16 @@ nyf_status run_batched(const nyf_batch_item* items, int B, int n, const nyf_para
     if (items[b].offset < 0 || items[b].H < 1 || items[b].W < 1) return NYF_ERR_INVALID_ARG;
   StreamPool* P = nullptr;
   if (device_pool(&P) != cudaSuccess) return NYF_ERR_CUDA;
+  cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
+  nyf_status status = pre(offs, total, caller);
+  if (status != NYF_OK) return status;
   std::vector<int> sof(B);
   assign_streams(items, B, sof.data());
   bool used[kPool] = {false};
   for (int b = 0; b < B; ++b) used[sof[b]] = true;
-  cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
   NYF_TRY(cudaEventRecord(P->fork, caller));
   for (int i = 0; i < kPool; ++i)
     if (used[i]) NYF_TRY(cudaStreamWaitEvent(P->s[i], P->fork, 0));
-  nyf_status status = NYF_OK;
   for (int b = 0; b < B && status == NYF_OK; ++b) {
     const nyf_params q = item_params(p, items[b]);
     status = per_image(b, q, reinterpret_cast<char*>(ws) + offs[b], total - offs[b], P->s[sof[b]]);
@@ -441,6 +486,81 @@ nyf_status run_batched(const nyf_batch_item* items, int B, int n, const nyf_para
   return status;
 }
 
+template <typename Fn>
+nyf_status run_batched(const nyf_batch_item* items, int B, int n, const nyf_params* p, void* ws,
+                       size_t ws_bytes, void* stream, Fn&& per_image) {
+  return run_batched(items, B, n, p, ws, ws_bytes, stream,
+                     [](const std::vector<size_t>&, size_t, cudaStream_t) { return NYF_OK; },
+                     per_image);
+}
+
+// Whether the batched forward runs its landmark and eigendecomposition steps as
+// stage-batched launches (every image's k-means on the CUDA-core assignment
+// pass over all of its rows, or landmarks given; a FIR or recursive window).
+bool staged_forward(const nyf_params* p, int n, const float* landmarks) {
+  return p->sample_frac >= 1.f && (landmarks || kmeans_batchable(n, p->K));
+}
+
+// Stage-batched forward: per image the checks and state reset, then the
+// landmarks of all images (k-means batch or copies), the eigendecompositions of
+// all images, then features + convolutions per image on the stream pool.  Every
+// image runs the kernels and reduction orders of nyf_filter_blf, so the results
+// are bitwise those of per-image calls.
+nyf_status blf_batched_forward(const float* f, const nyf_batch_item* items, int B, int n,
+                               const nyf_params* p, const float* landmarks, float* out, void* ws,
+                               size_t ws_bytes, void* stream) {
+  const int64_t lm_stride = (int64_t)p->K * n;
+  std::vector<nyf_params> qs(B);
+  std::vector<FwdCtx> ctx(B);
+  auto pre = [&](const std::vector<size_t>& offs, size_t total, cudaStream_t st) -> nyf_status {
+    for (int b = 0; b < B; ++b) {
+      const nyf_batch_item& it = items[b];
+      qs[b] = item_params(p, it);
+      nyf_status s = fwd_prepare(f + it.offset, nullptr, it.H, it.W, n, n, &qs[b], out + it.offset,
+                                 reinterpret_cast<char*>(ws) + offs[b], total - offs[b], &ctx[b]);
+      if (s != NYF_OK) return s;
+      if (p->K > ctx[b].N) return NYF_ERR_INVALID_ARG;
+    }
+    for (int b = 0; b < B; ++b) {
+      nyf_status s = fwd_reset(ctx[b], nullptr, st);
+      if (s != NYF_OK) return s;
+    }
+    if (landmarks) {
+      for (int b = 0; b < B; ++b)
+        NYF_TRY(cudaMemcpyAsync(ctx[b].w + ctx[b].L.landmarks, landmarks + b * lm_stride,
+                                sizeof(float) * lm_stride, cudaMemcpyDeviceToDevice, st));
+    } else {
+      std::vector<KmItem> km(B);
+      for (int b = 0; b < B; ++b) {
+        const FwdCtx& c = ctx[b];
+        km[b].X = c.guide;
+        km[b].N = c.N;
+        km[b].seed = qs[b].seed;
+        km[b].cent = reinterpret_cast<float*>(c.w + c.L.landmarks);
+        km[b].part = reinterpret_cast<float*>(c.w + c.L.km_part);
+        km[b].qpart = reinterpret_cast<float*>(c.w + c.L.km_qpart);
+        km[b].idx_out = reinterpret_cast<int64_t*>(c.w + c.L.init_idx);
+        km[b].state = c.state;
+      }
+      NYF_TRY(launch_kmeans_batched(km.data(), B, n, p->K, p->kmeans_iters, st));
+    }
+    std::vector<EigItem> eg(B);
+    for (int b = 0; b < B; ++b) {
+      const FwdCtx& c = ctx[b];
+      eg[b].landmarks = reinterpret_cast<const float*>(c.w + c.L.landmarks);
+      eg[b].sigma_r = qs[b].sigma_r;
+      eg[b].what = reinterpret_cast<float*>(c.w + c.L.what);
+      eg[b].state = c.state;
+      eg[b].scratch = c.w + c.L.eig;
+    }
+    NYF_TRY(launch_eig_batched(eg.data(), B, p->K, n, p->eig_rel_tol, st));
+    return NYF_OK;
+  };
+  return run_batched(items, B, n, p, ws, ws_bytes, stream, pre,
+                     [&](int b, const nyf_params&, void*, size_t, cudaStream_t s) {
+                       return fwd_finish(ctx[b], s, false);
+                     });
+}
 
 // ---- PCA-NLM: the joint-filter layout for a q-dimensional guide, then the
 // guide, the PCA outputs, a device state for the eigendecomposition and its scratch.
@@ -786,6 +906,8 @@ nyf_status nyf_filter_blf_batched(const float* f, const nyf_batch_item* items, i
                                   const nyf_params* p, const float* landmarks, float* out, void* ws,
                                   size_t ws_bytes, void* stream) {
   if (!f || !out || !p || (landmarks && !aligned4(landmarks))) return NYF_ERR_INVALID_ARG;
+  if (staged_forward(p, n, landmarks))
+    return blf_batched_forward(f, items, B, n, p, landmarks, out, ws, ws_bytes, stream);
   const int64_t lm_stride = (int64_t)p->K * n;
   return run_batched(items, B, n, p, ws, ws_bytes, stream,
                      [&](int b, const nyf_params& q, void* wsb, size_t wsn, cudaStream_t s) {

@@ -48,8 +48,38 @@ struct EigBuf {
   int bad;
 };
 
+// Arguments of one decomposition.  The kernels take them through a policy P:
+// EigOne (one problem per launch) or EigMany (a batch, problem = blockIdx.y), so
+// every problem of a batch runs exactly the code and order of a single launch.
+struct EigJob {
+  const float* lm;
+  double inv2s2;
+  EigBuf* b;
+  double* alphas;   // nullable
+  int* rank;        // nullable
+  DevState* state;
+  float* what;
+};
+struct EigOne {
+  EigJob j;
+  __device__ __forceinline__ const EigJob& get() const { return j; }
+};
+struct EigMany {
+  EigJob j[kBatchMax];
+  __device__ __forceinline__ const EigJob& get() const { return j[blockIdx.y]; }
+};
+
+template <class P>
+__global__ void k_eig_reset(const __grid_constant__ P p) {
+  if (threadIdx.x == 0) p.get().b->bad = 0;
+}
+
 // ---- 1. A in FP64, one column per CTA
-__global__ void k_a64(const float* __restrict__ lm, int K, int rho, double inv2s2, EigBuf* b) {
+template <class P>
+__global__ void k_a64(const __grid_constant__ P p, int K, int rho) {
+  const float* __restrict__ lm = p.get().lm;
+  const double inv2s2 = p.get().inv2s2;
+  EigBuf* b = p.get().b;
   const int j = blockIdx.x, i = threadIdx.x;
   __shared__ double red[kMaxK];
   double a = 0.0;
@@ -109,7 +139,9 @@ __device__ __forceinline__ int rr_player(int pos, int step, int Kp) {
   return pos == 0 ? 0 : 1 + (pos - 1 + step) % (Kp - 1);
 }
 
-__global__ void __launch_bounds__(kJacThreads) k_jacobi32(int K, EigBuf* b) {
+template <class P>
+__global__ void __launch_bounds__(kJacThreads) k_jacobi32(const __grid_constant__ P p, int K) {
+  EigBuf* b = p.get().b;
   extern __shared__ __align__(16) unsigned char raw[];
   Jac32& sm = *reinterpret_cast<Jac32*>(raw);
   const int tid = threadIdx.x;
@@ -211,7 +243,9 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi32(int K, EigBuf* b) {
 }
 
 // ---- 3a. Y = A X (column j per CTA)
-__global__ void k_oa_y(int K, int src, EigBuf* b) {
+template <class P>
+__global__ void k_oa_y(const __grid_constant__ P p, int K, int src) {
+  EigBuf* b = p.get().b;
   const int j = blockIdx.x, i = threadIdx.x;
   __shared__ double xj[kMaxK];
   if (i < K) xj[i] = b->X[src][i * K + j];
@@ -224,7 +258,9 @@ __global__ void k_oa_y(int K, int src, EigBuf* b) {
 }
 
 // ---- 3b. S = X^T Y, R = I - X^T X (column j per CTA) and their column norms
-__global__ void k_oa_sr(int K, int src, EigBuf* b) {
+template <class P>
+__global__ void k_oa_sr(const __grid_constant__ P p, int K, int src) {
+  EigBuf* b = p.get().b;
   const int j = blockIdx.x, i = threadIdx.x;
   __shared__ double xj[kMaxK], yj[kMaxK], rs[kMaxK], rr[kMaxK];
   const double* X = b->X[src];
@@ -260,7 +296,9 @@ __global__ void k_oa_sr(int K, int src, EigBuf* b) {
 }
 
 // ---- 3c. lam, E[:, j] and X_new[:, j] = X[:, j] + X E[:, j]
-__global__ void k_oa_update(int K, int src, int orth_only, EigBuf* b) {
+template <class P>
+__global__ void k_oa_update(const __grid_constant__ P p, int K, int src, int orth_only) {
+  EigBuf* b = p.get().b;
   const int j = blockIdx.x, i = threadIdx.x;
   __shared__ double lam[kMaxK], ej[kMaxK], cS[kMaxK], cR[kMaxK], cA[kMaxK];
   __shared__ double delta;
@@ -311,7 +349,9 @@ __global__ void k_oa_update(int K, int src, int orth_only, EigBuf* b) {
 // to the columns of X.  One warp; pairs are scanned in cyclic row order and a
 // pair rotates when |S_pq| > 4 eps sqrt(|S_pp S_qq|) (the negligibility test of
 // Demmel & Veselic).  Writes the eigenvalues to lam.
-__global__ void k_polish(int K, int src, EigBuf* b) {
+template <class P>
+__global__ void k_polish(const __grid_constant__ P p, int K, int src) {
+  EigBuf* b = p.get().b;
   extern __shared__ double ps[];
   double* Sm = ps;                     // K x (K + 1)
   double* Xm = ps + K * (K + 1);       // K x (K + 1)
@@ -391,8 +431,12 @@ __global__ void k_polish(int K, int src, EigBuf* b) {
 // feature stays close to one landmark's kernel column, so the sum over modes
 // in Eqs. (14)-(15) does not cancel large terms (it does with the eigenvector
 // factor, whose rounding then dominates the result in low precision).
-__global__ void k_finalize(int K, double tau, EigBuf* b, double* __restrict__ alphas_out,
-                           int* __restrict__ rank_out, DevState* state) {
+template <class P>
+__global__ void k_finalize(const __grid_constant__ P p, int K, double tau) {
+  EigBuf* b = p.get().b;
+  double* __restrict__ alphas_out = p.get().alphas;
+  int* __restrict__ rank_out = p.get().rank;
+  DevState* state = p.get().state;
   __shared__ double lam[kMaxK];
   const int tid = threadIdx.x;
   if (tid < K) lam[tid] = b->lam[tid];
@@ -428,7 +472,10 @@ __global__ void k_finalize(int K, double tau, EigBuf* b, double* __restrict__ al
 }
 
 // W_hat[m][j] = sum_{k < r} w_m,k w_j,k / sqrt(alpha_k)  (FP64, one column per CTA)
-__global__ void k_wsym(int K, int src, const EigBuf* b, float* __restrict__ what) {
+template <class P>
+__global__ void k_wsym(const __grid_constant__ P p, int K, int src) {
+  const EigBuf* b = p.get().b;
+  float* __restrict__ what = p.get().what;
   const int j = blockIdx.x, m = threadIdx.x;
   __shared__ double cj[kMaxK];
   const double* X = b->X[src];
@@ -451,47 +498,86 @@ size_t eig_scratch_bytes() { return sizeof(EigBuf); }
 
 const double* eig_A64(const void* scratch) { return reinterpret_cast<const EigBuf*>(scratch)->A; }
 
-cudaError_t launch_eig(const float* landmarks, int K, int rho, float sigma_r, double tau,
-                       float* what, double* alphas_out, int* rank_out, DevState* state,
-                       void* scratch, cudaStream_t st) {
-  EigBuf* b = reinterpret_cast<EigBuf*>(scratch);
-  cudaError_t e = cudaMemsetAsync(&b->bad, 0, sizeof(int), st);
+namespace {
+
+// The sequence of launches of the decomposition for `count` problems (grid.y).
+template <class P>
+cudaError_t eig_run(const P& p, int count, int K, int rho, double tau, cudaStream_t st) {
+  const dim3 one(1, count), cols(K, count);
+  k_eig_reset<P><<<one, 32, 0, st>>>(p);
+  k_a64<P><<<cols, kMaxK, 0, st>>>(p, K, rho);
+  count_launches(2);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const double inv2s2 = 1.0 / (2.0 * (double)sigma_r * (double)sigma_r);
-  k_a64<<<K, kMaxK, 0, st>>>(landmarks, K, rho, inv2s2, b);
-  count_launches(1);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const size_t smem = sizeof(Jac32);
-  e = cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(k_jacobi32<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_jacobi32<<<1, kJacThreads, smem, st>>>(K, b);
+  k_jacobi32<P><<<one, kJacThreads, smem, st>>>(p, K);
   count_launches(1);
   int src = 0;
   for (int it = 0; it < kRefineIters; ++it) {
-    k_oa_y<<<K, kMaxK, 0, st>>>(K, src, b);
-    k_oa_sr<<<K, kMaxK, 0, st>>>(K, src, b);
-    k_oa_update<<<K, kMaxK, 0, st>>>(K, src, 0, b);
+    k_oa_y<P><<<cols, kMaxK, 0, st>>>(p, K, src);
+    k_oa_sr<P><<<cols, kMaxK, 0, st>>>(p, K, src);
+    k_oa_update<P><<<cols, kMaxK, 0, st>>>(p, K, src, 0);
     count_launches(3);
     src ^= 1;
   }
   // orthonormalise once more (X <- X (I + R / 2), second-order accurate), then
   // S = X^T A X for the polish
-  k_oa_y<<<K, kMaxK, 0, st>>>(K, src, b);
-  k_oa_sr<<<K, kMaxK, 0, st>>>(K, src, b);
-  k_oa_update<<<K, kMaxK, 0, st>>>(K, src, 1, b);
+  k_oa_y<P><<<cols, kMaxK, 0, st>>>(p, K, src);
+  k_oa_sr<P><<<cols, kMaxK, 0, st>>>(p, K, src);
+  k_oa_update<P><<<cols, kMaxK, 0, st>>>(p, K, src, 1);
   src ^= 1;
-  k_oa_y<<<K, kMaxK, 0, st>>>(K, src, b);
-  k_oa_sr<<<K, kMaxK, 0, st>>>(K, src, b);
-  count_launches(3);
+  k_oa_y<P><<<cols, kMaxK, 0, st>>>(p, K, src);
+  k_oa_sr<P><<<cols, kMaxK, 0, st>>>(p, K, src);
+  count_launches(5);
   const size_t psmem = sizeof(double) * 2 * K * (K + 1);
-  e = cudaFuncSetAttribute(k_polish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+  e = cudaFuncSetAttribute(k_polish<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
   if (e != cudaSuccess) return e;
-  k_polish<<<1, 32, psmem, st>>>(K, src, b);
+  k_polish<P><<<one, 32, psmem, st>>>(p, K, src);
+  k_finalize<P><<<one, kMaxK, 0, st>>>(p, K, tau);
+  k_wsym<P><<<cols, kMaxK, 0, st>>>(p, K, src);
   count_launches(3);
-  k_finalize<<<1, kMaxK, 0, st>>>(K, tau, b, alphas_out, rank_out, state);
-  k_wsym<<<K, kMaxK, 0, st>>>(K, src, b, what);
-  count_launches(2);
   return cudaGetLastError();
+}
+
+EigJob make_job(const float* landmarks, float sigma_r, float* what, double* alphas_out,
+                int* rank_out, DevState* state, void* scratch) {
+  EigJob j;
+  j.lm = landmarks;
+  j.inv2s2 = 1.0 / (2.0 * (double)sigma_r * (double)sigma_r);
+  j.b = reinterpret_cast<EigBuf*>(scratch);
+  j.alphas = alphas_out;
+  j.rank = rank_out;
+  j.state = state;
+  j.what = what;
+  return j;
+}
+
+}  // namespace
+
+cudaError_t launch_eig(const float* landmarks, int K, int rho, float sigma_r, double tau,
+                       float* what, double* alphas_out, int* rank_out, DevState* state,
+                       void* scratch, cudaStream_t st) {
+  EigOne p;
+  p.j = make_job(landmarks, sigma_r, what, alphas_out, rank_out, state, scratch);
+  return eig_run(p, 1, K, rho, tau, st);
+}
+
+cudaError_t launch_eig_batched(const EigItem* items, int count, int K, int rho, double tau,
+                               cudaStream_t st) {
+  for (int b0 = 0; b0 < count; b0 += kBatchMax) {
+    const int m = count - b0 < kBatchMax ? count - b0 : kBatchMax;
+    EigMany p;
+    for (int i = 0; i < m; ++i) {
+      const EigItem& it = items[b0 + i];
+      p.j[i] = make_job(it.landmarks, it.sigma_r, it.what, nullptr, nullptr, it.state, it.scratch);
+    }
+    for (int i = m; i < kBatchMax; ++i) p.j[i] = p.j[0];
+    cudaError_t e = eig_run(p, m, K, rho, tau, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace nyf

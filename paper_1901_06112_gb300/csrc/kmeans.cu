@@ -44,9 +44,16 @@ __global__ void k_sample_rows(const float* __restrict__ G, int64_t N, int rho, i
 // Centroids are stored with row stride 4 (float4, zero padded) when rho <= 4.
 __host__ __device__ constexpr int mu_stride(int rho) { return rho <= 4 ? 4 : rho; }
 
+// Rows of rho <= 4 also keep the negated centroids as duplicated pairs
+// (-mu_jd, -mu_jd), d < 4, for the packed distance loop.
+__host__ __device__ constexpr size_t neg_pairs_offset(int K, int rho, int warps) {
+  return ((size_t)K * mu_stride(rho) + (size_t)warps * K * (rho + 1) + 3) & ~(size_t)3;
+}
+
 size_t assign_smem(int K, int rho) {
   const int warps = assign_threads(rho <= 32 ? 1 : 0) / 32;
-  return sizeof(float) * ((size_t)K * mu_stride(rho) + (size_t)warps * K * (rho + 1));
+  const size_t pairs = rho <= 4 ? (size_t)K * 8 : 0;
+  return sizeof(float) * (neg_pairs_offset(K, rho, warps) + pairs);
 }
 
 int kmeans_grid(int64_t N, int rho) {
@@ -64,11 +71,63 @@ __device__ inline int reflect101(int i, int n) {
   return j < n ? j : period - j;
 }
 
+// Arguments of one clustering problem.  The kernels take them through a policy
+// P: KmOne (one problem per launch) or KmMany (a batch; the assignment pass maps
+// its flat block index to (problem, block) through the prefix sums `first`, the
+// other kernels take the problem from blockIdx.y), so every problem of a batch
+// runs exactly the code, grid partition and reduction order of a single launch.
+struct KmJob {
+  const float* X;
+  int64_t N;
+  float* cent;
+  int32_t* labels;          // nullable
+  float* part;
+  float* qpart;
+  double* qerr_out;         // nullable
+  const int64_t* init_idx;  // nullable
+  int64_t* idx_out;
+  DevState* state;
+  uint64_t seed;
+  int grid;                 // blocks of this problem's assignment pass
+};
+struct KmOne {
+  KmJob j;
+  __device__ __forceinline__ const KmJob& get() const { return j; }
+  __device__ __forceinline__ const KmJob& job_for_block(int& blk) const {
+    blk = blockIdx.x;
+    return j;
+  }
+};
+struct KmMany {
+  int count;
+  int first[kBatchMax + 1];
+  KmJob j[kBatchMax];
+  __device__ __forceinline__ const KmJob& get() const { return j[blockIdx.y]; }
+  __device__ __forceinline__ const KmJob& job_for_block(int& blk) const {
+    const int x = blockIdx.x;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (first[mid] <= x) lo = mid;
+      else hi = mid - 1;
+    }
+    blk = x - first[lo];
+    return j[lo];
+  }
+};
+
 // Initial centroids: rows init_idx[j] of X, or the first K distinct values of
 // SplitMix64(seed) mod N (bounded number of draws).
-__global__ void k_draw_init(const float* __restrict__ X, int64_t N, int rho, int K, uint64_t seed,
-                            const int64_t* __restrict__ init_idx, int64_t* __restrict__ idx_out,
-                            float* __restrict__ cent, DevState* state) {
+template <class P>
+__global__ void k_draw_init(const __grid_constant__ P p, int rho, int K) {
+  const KmJob& J = p.get();
+  const float* __restrict__ X = J.X;
+  const int64_t N = J.N;
+  const uint64_t seed = J.seed;
+  const int64_t* __restrict__ init_idx = J.init_idx;
+  int64_t* __restrict__ idx_out = J.idx_out;
+  float* __restrict__ cent = J.cent;
+  DevState* state = J.state;
   __shared__ int64_t idx[kMaxK];
   __shared__ int ok;
   if (threadIdx.x == 0) {
@@ -112,6 +171,57 @@ __device__ __forceinline__ void unpack_rows(const float* buf, float (&x)[PPT][RX
     for (int d = 0; d < RX; ++d) x[q][d] = d < R ? buf[q * R + d] : 0.f;
 }
 
+// Nearest centroid of the PPT rows in x (R <= 4 coordinates; mu: centroids with
+// row stride 4; nmu2: (-mu_jd, -mu_jd) pairs, 8 floats per centroid).  Rows are
+// evaluated two at a time in packed FP32x2: t = x + (-mu), dist = sum of t^2 in
+// coordinate order.  The running minimum is kept as a key, the distance's bit
+// pattern (non-negative, so ordered like the value) with its six low mantissa
+// bits replaced by j: one integer minimum per row and centroid, ties (and
+// distances equal to within 2^-17 relative) to the lowest index.  The chosen
+// centroid's distance is then formed again, exactly as in the loop.
+template <int R, int PPT>
+__device__ __forceinline__ void nearest_small(const float (&x)[PPT][4], const float* mu,
+                                              const float* nmu2, int K, int (&best)[PPT],
+                                              float (&bd)[PPT]) {
+  static_assert(PPT % 2 == 0 && R >= 1 && R <= 4, "row pairs, at most 4 coordinates");
+  static_assert(kMaxK <= 64, "the centroid index fits the six low bits of a key");
+  unsigned key[PPT];
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) key[q] = 0xffffffffu;
+#pragma unroll 4
+  for (int j = 0; j < K; ++j) {
+    const float4 n01 = *reinterpret_cast<const float4*>(nmu2 + 8 * j);
+    const float4 n23 = *reinterpret_cast<const float4*>(nmu2 + 8 * j + 4);
+    const float2 nc[4] = {make_float2(n01.x, n01.y), make_float2(n01.z, n01.w),
+                          make_float2(n23.x, n23.y), make_float2(n23.z, n23.w)};
+#pragma unroll
+    for (int pr = 0; pr < PPT / 2; ++pr) {
+      float2 t = __fadd2_rn(make_float2(x[2 * pr][0], x[2 * pr + 1][0]), nc[0]);
+      float2 dist = __fmul2_rn(t, t);
+#pragma unroll
+      for (int d = 1; d < R; ++d) {
+        t = __fadd2_rn(make_float2(x[2 * pr][d], x[2 * pr + 1][d]), nc[d]);
+        dist = __ffma2_rn(t, t, dist);
+      }
+      key[2 * pr] = min(key[2 * pr], (__float_as_uint(dist.x) & ~63u) | (unsigned)j);
+      key[2 * pr + 1] = min(key[2 * pr + 1], (__float_as_uint(dist.y) & ~63u) | (unsigned)j);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    best[q] = (int)(key[q] & 63u);
+    const float* c = mu + 4 * best[q];
+    float t = x[q][0] + (-c[0]);
+    float dist = t * t;
+#pragma unroll
+    for (int d = 1; d < R; ++d) {
+      t = x[q][d] + (-c[d]);
+      dist = fmaf(t, t, dist);
+    }
+    bd[q] = dist;
+  }
+}
+
 // Assignment pass.  RB > 0: each thread holds PPT consecutive rows in
 // registers (rho <= RB), so one centroid load from shared memory serves PPT
 // distance evaluations, evaluated two rows at a time with packed FP32x2
@@ -125,11 +235,18 @@ __device__ __forceinline__ void unpack_rows(const float* buf, float (&x)[PPT][RX
 // part[b][j][rho] = their count; qpart[b] = sum of their squared distances.
 // Every sum runs in an order fixed by the data layout, so results are bitwise
 // reproducible.
-template <int RB, int THREADS, int PPT>
+template <class P, int RB, int THREADS, int PPT>
 __global__ void __launch_bounds__(THREADS)
-k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __restrict__ cent,
-         int32_t* __restrict__ labels, float* __restrict__ part, float* __restrict__ qpart,
-         int accumulate) {
+k_assign(const __grid_constant__ P p, int rho, int K, int accumulate) {
+  int blk;
+  const KmJob& J = p.job_for_block(blk);
+  const int nblk = J.grid;
+  const float* __restrict__ X = J.X;
+  const int64_t N = J.N;
+  const float* __restrict__ cent = J.cent;
+  int32_t* __restrict__ labels = J.labels;
+  float* __restrict__ part = J.part;
+  float* __restrict__ qpart = J.qpart;
   extern __shared__ __align__(16) float sm[];
   constexpr int kWarps = THREADS / 32;
   constexpr int RX = RB > 0 ? RB : 1;
@@ -142,14 +259,22 @@ k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __
     const int j = e / ms, d = e - j * ms;
     mu[e] = d < rho ? cent[j * rho + d] : 0.f;
   }
+  float* nmu2 = sm + neg_pairs_offset(K, rho, kWarps);   // rho <= 4 only
+  if (RB == 4)
+    for (int e = tid; e < K * 4; e += blockDim.x) {
+      const int j = e / 4, d = e - j * 4;
+      const float v = d < rho ? -cent[j * rho + d] : 0.f;
+      nmu2[8 * j + 2 * d] = v;
+      nmu2[8 * j + 2 * d + 1] = v;
+    }
   if (accumulate)
     for (int e = tid; e < kWarps * K * stride; e += blockDim.x) acc[e] = 0.f;
   __syncthreads();
 
   float qsum = 0.f;
   if (RB > 0) {
-    for (int64_t base = (int64_t)blockIdx.x * THREADS * PPT; base < N;
-         base += (int64_t)gridDim.x * THREADS * PPT) {
+    for (int64_t base = (int64_t)blk * THREADS * PPT; base < N;
+         base += (int64_t)nblk * THREADS * PPT) {
       const int64_t i0 = base + (int64_t)tid * PPT;       // this thread's first row
       float x[PPT][RX];
       bool valid[PPT];
@@ -191,6 +316,15 @@ k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __
         best[q] = 0;
         bd[q] = __int_as_float(0x7f800000);
       }
+      if constexpr (RB == 4 && PPT % 2 == 0) {
+        const float (&x4)[PPT][4] = reinterpret_cast<const float (&)[PPT][4]>(x);
+        switch (rho) {
+          case 1: nearest_small<1, PPT>(x4, mu, nmu2, K, best, bd); break;
+          case 2: nearest_small<2, PPT>(x4, mu, nmu2, K, best, bd); break;
+          case 3: nearest_small<3, PPT>(x4, mu, nmu2, K, best, bd); break;
+          default: nearest_small<4, PPT>(x4, mu, nmu2, K, best, bd); break;
+        }
+      } else {
 #pragma unroll 4
       for (int j = 0; j < K; ++j) {
         const float* m = mu + j * ms;
@@ -231,6 +365,7 @@ k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __
           }
           if (dist < bd[0]) { bd[0] = dist; best[0] = j; }
         }
+      }
       }
 #pragma unroll
       for (int q = 0; q < PPT; ++q)
@@ -292,7 +427,7 @@ k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __
       }
     }
   } else {
-    for (int64_t base = (int64_t)blockIdx.x * THREADS; base < N; base += (int64_t)gridDim.x * THREADS) {
+    for (int64_t base = (int64_t)blk * THREADS; base < N; base += (int64_t)nblk * THREADS) {
       const int64_t i = base + tid;
       const bool valid = i < N;
       const float* xi = X + (valid ? i : 0) * rho;
@@ -334,7 +469,7 @@ k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __
     for (int e = tid; e < K * stride; e += blockDim.x) {
       float s = 0.f;
       for (int w = 0; w < kWarps; ++w) s += acc[w * K * stride + e];
-      part[(int64_t)blockIdx.x * K * stride + e] = s;
+      part[(int64_t)blk * K * stride + e] = s;
     }
   }
   __shared__ float qs[kWarps];
@@ -344,7 +479,7 @@ k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __
   if (tid == 0) {
     float s = 0.f;
     for (int w = 0; w < kWarps; ++w) s += qs[w];
-    qpart[blockIdx.x] = s;
+    qpart[blk] = s;
   }
 }
 
@@ -353,8 +488,12 @@ k_assign(const float* __restrict__ X, int64_t N, int rho, int K, const float* __
 // rho + 1 sums run side by side: thread (g, d) sums partials b = g, g + G, ...
 // of coordinate d (d = rho is the count), then thread d adds the G group sums
 // in order.
-__global__ void __launch_bounds__(256)
-k_update(const float* __restrict__ part, int nblk, int rho, int K, float* __restrict__ cent) {
+template <class P>
+__global__ void __launch_bounds__(256) k_update(const __grid_constant__ P p, int rho, int K) {
+  const KmJob& J = p.get();
+  const float* __restrict__ part = J.part;
+  const int nblk = J.grid;
+  float* __restrict__ cent = J.cent;
   __shared__ double red[256];
   __shared__ double sum[kMaxRho + 1];
   const int j = blockIdx.x, tid = threadIdx.x, stride = rho + 1;
@@ -423,8 +562,13 @@ __global__ void k_gather_rows(const float* __restrict__ X, int64_t N, int rho, i
 }
 
 // Quantisation error e = sum of the block partials (FP64, fixed order).
-__global__ void k_qerr(const float* __restrict__ qpart, int nblk, double* __restrict__ out,
-                       DevState* state) {
+template <class P>
+__global__ void k_qerr(const __grid_constant__ P p) {
+  const KmJob& J = p.get();
+  const float* __restrict__ qpart = J.qpart;
+  const int nblk = J.grid;
+  double* __restrict__ out = J.qerr_out;
+  DevState* state = J.state;
   __shared__ double red[256];
   const int tid = threadIdx.x;
   double s = 0.0;
@@ -467,29 +611,45 @@ __global__ void k_nlm_sample(const float* __restrict__ f, int H, int W, int n, i
   }
 }
 
-template <int RB>
-cudaError_t assign_launch(int grid, const float* X, int64_t N, int rho, int K, const float* cent,
-                          int32_t* labels, float* part, float* qpart, int accumulate,
-                          cudaStream_t st) {
+template <class P, int RB>
+cudaError_t assign_launch(const P& p, int grid, int rho, int K, int accumulate, cudaStream_t st) {
   constexpr int T = assign_threads(RB);
   constexpr int PPT = assign_ppt(RB);
   const size_t smem = assign_smem(K, rho);
-  cudaError_t e = cudaFuncSetAttribute(k_assign<RB, T, PPT>,
+  cudaError_t e = cudaFuncSetAttribute(k_assign<P, RB, T, PPT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_assign<RB, T, PPT><<<grid, T, smem, st>>>(X, N, rho, K, cent, labels, part, qpart, accumulate);
+  k_assign<P, RB, T, PPT><<<grid, T, smem, st>>>(p, rho, K, accumulate);
   count_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t assign_dispatch(int grid, const float* X, int64_t N, int rho, int K,
-                            const float* cent, int32_t* labels, float* part, float* qpart,
-                            int accumulate, cudaStream_t st) {
-  if (rho <= 4) return assign_launch<4>(grid, X, N, rho, K, cent, labels, part, qpart, accumulate, st);
-  if (rho <= 8) return assign_launch<8>(grid, X, N, rho, K, cent, labels, part, qpart, accumulate, st);
-  if (rho <= 16) return assign_launch<16>(grid, X, N, rho, K, cent, labels, part, qpart, accumulate, st);
-  if (rho <= 32) return assign_launch<32>(grid, X, N, rho, K, cent, labels, part, qpart, accumulate, st);
-  return assign_launch<0>(grid, X, N, rho, K, cent, labels, part, qpart, accumulate, st);
+// grid: total blocks of the launch (the sum of the problems' grids for KmMany)
+template <class P>
+cudaError_t assign_dispatch(const P& p, int grid, int rho, int K, int accumulate, cudaStream_t st) {
+  if (rho <= 4) return assign_launch<P, 4>(p, grid, rho, K, accumulate, st);
+  if (rho <= 8) return assign_launch<P, 8>(p, grid, rho, K, accumulate, st);
+  if (rho <= 16) return assign_launch<P, 16>(p, grid, rho, K, accumulate, st);
+  if (rho <= 32) return assign_launch<P, 32>(p, grid, rho, K, accumulate, st);
+  return assign_launch<P, 0>(p, grid, rho, K, accumulate, st);
+}
+
+KmJob make_job(const float* X, int64_t N, int rho, float* cent, int32_t* labels, float* part,
+               float* qpart, double* qerr_out, DevState* state) {
+  KmJob j;
+  j.X = X;
+  j.N = N;
+  j.cent = cent;
+  j.labels = labels;
+  j.part = part;
+  j.qpart = qpart;
+  j.qerr_out = qerr_out;
+  j.init_idx = nullptr;
+  j.idx_out = nullptr;
+  j.state = state;
+  j.seed = 0;
+  j.grid = kmeans_grid(N, rho);
+  return j;
 }
 
 }  // namespace
@@ -499,7 +659,12 @@ size_t kmeans_smem_bytes(int K, int rho) { return assign_smem(K, rho); }
 cudaError_t launch_draw_init(const float* X, int64_t N, int rho, int K, uint64_t seed,
                              const int64_t* init_idx, int64_t* idx_out, float* centroids,
                              DevState* state, cudaStream_t st) {
-  k_draw_init<<<1, 256, 0, st>>>(X, N, rho, K, seed, init_idx, idx_out, centroids, state);
+  KmOne p;
+  p.j = make_job(X, N, rho, centroids, nullptr, nullptr, nullptr, nullptr, state);
+  p.j.seed = seed;
+  p.j.init_idx = init_idx;
+  p.j.idx_out = idx_out;
+  k_draw_init<KmOne><<<1, 256, 0, st>>>(p, rho, K);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -507,52 +672,100 @@ cudaError_t launch_draw_init(const float* X, int64_t N, int rho, int K, uint64_t
 cudaError_t launch_kmeans(const float* X, int64_t N, int rho, int K, int iters, float* centroids,
                           int32_t* labels, double* qerr_out, float* part, float* qpart,
                           DevState* state, cudaStream_t st) {
+  KmOne p;
+  p.j = make_job(X, N, rho, centroids, nullptr, part, qpart, qerr_out, state);
   if (assign_tc_supported(rho, K)) {   // rows deep enough for the tensor cores
     const int grid = assign_tc_grid(N);
+    p.j.grid = grid;
     for (int it = 0; it < iters; ++it) {
       cudaError_t e = launch_assign_tc(grid, X, N, rho, K, centroids, nullptr, part, qpart, 1,
                                        state, st);
       if (e != cudaSuccess) return e;
-      k_update<<<K, 256, 0, st>>>(part, grid, rho, K, centroids);
+      k_update<KmOne><<<K, 256, 0, st>>>(p, rho, K);
       count_launches(1);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     cudaError_t e = launch_assign_tc(grid, X, N, rho, K, centroids, labels, part, qpart, 0, state, st);
     if (e != cudaSuccess) return e;
-    k_qerr<<<1, 256, 0, st>>>(qpart, grid, qerr_out, state);
+    k_qerr<KmOne><<<1, 256, 0, st>>>(p);
     count_launches(1);
     return cudaGetLastError();
   }
   const int grid = kmeans_grid(N, rho);
+  p.j.grid = grid;
   for (int it = 0; it < iters; ++it) {
-    cudaError_t e = assign_dispatch(grid, X, N, rho, K, centroids, nullptr, part, qpart, 1, st);
+    cudaError_t e = assign_dispatch(p, grid, rho, K, 1, st);
     if (e != cudaSuccess) return e;
-    k_update<<<K, 256, 0, st>>>(part, grid, rho, K, centroids);
+    k_update<KmOne><<<K, 256, 0, st>>>(p, rho, K);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  cudaError_t e = assign_dispatch(grid, X, N, rho, K, centroids, labels, part, qpart, 0, st);
+  p.j.labels = labels;
+  cudaError_t e = assign_dispatch(p, grid, rho, K, 0, st);
   if (e != cudaSuccess) return e;
-  k_qerr<<<1, 256, 0, st>>>(qpart, grid, qerr_out, state);
+  k_qerr<KmOne><<<1, 256, 0, st>>>(p);
   count_launches(1);
   return cudaGetLastError();
+}
+
+bool kmeans_batchable(int rho, int K) { return !assign_tc_supported(rho, K); }
+
+cudaError_t launch_kmeans_batched(const KmItem* items, int count, int rho, int K, int iters,
+                                  cudaStream_t st) {
+  if (!kmeans_batchable(rho, K)) return cudaErrorInvalidValue;
+  for (int b0 = 0; b0 < count; b0 += kBatchMax) {
+    const int m = count - b0 < kBatchMax ? count - b0 : kBatchMax;
+    KmMany p;
+    p.count = m;
+    int total = 0;
+    for (int i = 0; i < kBatchMax; ++i) {
+      const KmItem& it = items[b0 + (i < m ? i : 0)];
+      p.j[i] = make_job(it.X, it.N, rho, it.cent, nullptr, it.part, it.qpart, nullptr, it.state);
+      p.j[i].seed = it.seed;
+      p.j[i].idx_out = it.idx_out;
+      if (i < m) {
+        p.first[i] = total;
+        total += p.j[i].grid;
+      }
+    }
+    p.first[m] = total;
+    const dim3 one(1, m), clusters(K, m);
+    k_draw_init<KmMany><<<one, 256, 0, st>>>(p, rho, K);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int it = 0; it < iters; ++it) {
+      if ((e = assign_dispatch(p, total, rho, K, 1, st)) != cudaSuccess) return e;
+      k_update<KmMany><<<clusters, 256, 0, st>>>(p, rho, K);
+      count_launches(1);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = assign_dispatch(p, total, rho, K, 0, st)) != cudaSuccess) return e;
+    k_qerr<KmMany><<<one, 256, 0, st>>>(p);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_kmeans_partials(const float* X, int64_t N, int rho, int K, const float* cent,
                                    double* sums, double* qerr, float* part, float* qpart,
                                    DevState* state, cudaStream_t st) {
   cudaError_t e;
+  KmOne p;
+  p.j = make_job(X, N, rho, const_cast<float*>(cent), nullptr, part, qpart, qerr, state);
   int grid;
   if (assign_tc_supported(rho, K)) {
     grid = assign_tc_grid(N);
     e = launch_assign_tc(grid, X, N, rho, K, cent, nullptr, part, qpart, 1, state, st);
   } else {
     grid = kmeans_grid(N, rho);
-    e = assign_dispatch(grid, X, N, rho, K, cent, nullptr, part, qpart, 1, st);
+    e = assign_dispatch(p, grid, rho, K, 1, st);
   }
   if (e != cudaSuccess) return e;
+  p.j.grid = grid;
   k_sums<<<K, 256, 0, st>>>(part, grid, rho, K, sums);
-  k_qerr<<<1, 256, 0, st>>>(qpart, grid, qerr, state);
+  k_qerr<KmOne><<<1, 256, 0, st>>>(p);
   count_launches(2);
   return cudaGetLastError();
 }

@@ -99,6 +99,37 @@ cudaError_t launch_eig(const float* landmarks, int K, int rho, float sigma_r, do
                        float* what, double* alphas_out, int* rank_out, DevState* state,
                        void* scratch, cudaStream_t st);
 size_t eig_scratch_bytes();
+// Stage-batched launches: one launch per step for a batch of independent
+// problems (the images of nyf_filter_blf_batched), problem b reading and
+// writing only its own buffers.  Each problem runs the code and reduction
+// order of a single-problem launch, so the results are bitwise those of
+// per-problem calls.  Batches above kBatchMax problems go in slices.
+constexpr int kBatchMax = 64;
+struct EigItem {
+  const float* landmarks;
+  float sigma_r;
+  float* what;
+  DevState* state;
+  void* scratch;
+};
+// k-means of a batch (Algorithm 1, clustering step, per problem): the initial
+// draw, `iters` Lloyd iterations and the final error pass, one launch per step.
+// Only for rows on the CUDA-core assignment pass (kmeans_batchable).
+struct KmItem {
+  const float* X;
+  int64_t N;
+  uint64_t seed;
+  float* cent;
+  float* part;
+  float* qpart;
+  int64_t* idx_out;
+  DevState* state;
+};
+bool kmeans_batchable(int rho, int K);
+cudaError_t launch_kmeans_batched(const KmItem* items, int count, int rho, int K, int iters,
+                                  cudaStream_t st);
+cudaError_t launch_eig_batched(const EigItem* items, int count, int K, int rho, double tau,
+                               cudaStream_t st);
 cudaError_t launch_features(const float* guide, int64_t N, int rho, const float* landmarks, int K,
                             float sigma_r, const float* what, const DevState* state, void* phi,
                             bool bf16, cudaStream_t st);
