@@ -30,7 +30,7 @@
 namespace nyf {
 namespace {
 
-constexpr int kJacThreads = 256;
+constexpr int kJacThreads = 512;
 constexpr int kMaxSweeps32 = 16;
 constexpr int kRefineIters = 3;
 
@@ -140,7 +140,7 @@ __device__ __forceinline__ int rr_player(int pos, int step, int Kp) {
 }
 
 template <class P>
-__global__ void __launch_bounds__(kJacThreads) k_jacobi32(const __grid_constant__ P p, int K) {
+__global__ void __launch_bounds__(kJacThreads, 1) k_jacobi32(const __grid_constant__ P p, int K) {
   EigBuf* b = p.get().b;
   extern __shared__ __align__(16) unsigned char raw[];
   Jac32& sm = *reinterpret_cast<Jac32*>(raw);
@@ -155,6 +155,23 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi32(const __grid_constant_
   __syncthreads();
   const float diag2 = block_sum_f(tid < K ? sm.A[tid][tid] * sm.A[tid][tid] : 0.f, sm.red);
   float prev = INFINITY;
+  // this thread's 2 x 2 blocks (pair u, pair v) of A and (row i, pair v) entries of V:
+  // fixed for the whole kernel, so the steps carry no integer divisions
+  constexpr int kMaxBlocks = (kMaxK / 2) * (kMaxK / 2) / kJacThreads;
+  constexpr int kMaxCols = kMaxK * (kMaxK / 2) / kJacThreads;
+  int bu[kMaxBlocks], bv[kMaxBlocks], ci[kMaxCols], cv[kMaxCols];
+#pragma unroll
+  for (int m = 0; m < kMaxBlocks; ++m) {
+    const int e = tid + m * kJacThreads;
+    bu[m] = e < half * half ? e / half : -1;
+    bv[m] = e - (e / half) * half;
+  }
+#pragma unroll
+  for (int m = 0; m < kMaxCols; ++m) {
+    const int e = tid + m * kJacThreads;
+    ci[m] = e < K * half ? e / half : -1;
+    cv[m] = e - (e / half) * half;
+  }
   if (b->bad == 0) {
     for (int sweep = 0; sweep < kMaxSweeps32; ++sweep) {
       float off = 0.f;
@@ -178,8 +195,11 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi32(const __grid_constant_
             // entries below FP32 resolution of the diagonal (subnormal ones included) are
             // not rotated, so that theta stays finite
             if (fabsf(apq) > 1e-30f * (fabsf(app) + fabsf(aqq)) && fabsf(apq) > 1e-36f) {
-              const float theta = (aqq - app) / (2.f * apq);
-              const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(1.f + theta * theta));
+              // fast divisions: |2 a_pq| is a normal number here, and an infinite theta
+              // gives t = 0 (no rotation); the FP64 refinement makes the start exact
+              const float theta = __fdividef(aqq - app, 2.f * apq);
+              const float t = (theta >= 0.f ? 1.f : -1.f) *
+                              __fdividef(1.f, fabsf(theta) + sqrtf(1.f + theta * theta));
               c = rsqrtf(1.f + t * t);
               s = t * c;
             }
@@ -192,44 +212,50 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi32(const __grid_constant_
           sm.s[tid] = s;
         }
         __syncthreads();
-        // 2 x 2 blocks of A: rows of pair u, columns of pair v
-        for (int e = tid; e < half * half; e += kJacThreads) {
-          const int u = e / half, v = e - u * half;
-          const int pu = sm.p[u], qu = sm.q[u], pv = sm.p[v], qv = sm.q[v];
-          const float cu = sm.c[u], su = sm.s[u], cv = sm.c[v], sv = sm.s[v];
-          const float a00 = sm.A[pu][pv], a01 = sm.A[pu][qv];
-          const float a10 = sm.A[qu][pv], a11 = sm.A[qu][qv];
-          // rows: [r0; r1] = R_u^T [a0.; a1.]
-          const float r00 = cu * a00 - su * a10, r01 = cu * a01 - su * a11;
-          const float r10 = su * a00 + cu * a10, r11 = su * a01 + cu * a11;
-          // columns: [.0 .1] = [r.0 r.1] R_v
-          const float n00 = cv * r00 - sv * r01, n01 = sv * r00 + cv * r01;
-          const float n10 = cv * r10 - sv * r11, n11 = sv * r10 + cv * r11;
-          if (pu == qu && pv == qv) {
-            sm.A[pu][pv] = n00;
-          } else if (pu == qu) {
-            sm.A[pu][pv] = n00;
-            sm.A[pu][qv] = n01;
-          } else if (pv == qv) {
-            sm.A[pu][pv] = n00;
-            sm.A[qu][pv] = n10;
-          } else {
-            sm.A[pu][pv] = n00;
-            sm.A[pu][qv] = n01;
-            sm.A[qu][pv] = n10;
-            sm.A[qu][qv] = n11;
-            if (u == v) sm.A[pu][qv] = sm.A[qu][pv] = 0.f;   // the annihilated entry
+        // 2 x 2 blocks of A (rows of pair u, columns of pair v) and the columns of V
+        // of pair v.  Distinct blocks touch distinct entries, so every thread first
+        // loads all of its blocks, then writes them: one shared-memory latency per
+        // step instead of one per block.
+#pragma unroll
+        for (int m = 0; m < kMaxBlocks; ++m) {
+          if (bu[m] >= 0) {
+            const int u = bu[m], v = bv[m];
+            const int pu = sm.p[u], qu = sm.q[u], pv = sm.p[v], qv = sm.q[v];
+            const float cu = sm.c[u], su = sm.s[u], cv = sm.c[v], sv = sm.s[v];
+            const float a00 = sm.A[pu][pv], a01 = sm.A[pu][qv];
+            const float a10 = sm.A[qu][pv], a11 = sm.A[qu][qv];
+            const float r00 = cu * a00 - su * a10, r01 = cu * a01 - su * a11;
+            const float r10 = su * a00 + cu * a10, r11 = su * a01 + cu * a11;
+            const float n00 = cv * r00 - sv * r01, n01 = sv * r00 + cv * r01;
+            const float n10 = cv * r10 - sv * r11, n11 = sv * r10 + cv * r11;
+            if (pu == qu && pv == qv) {
+              sm.A[pu][pv] = n00;
+            } else if (pu == qu) {
+              sm.A[pu][pv] = n00;
+              sm.A[pu][qv] = n01;
+            } else if (pv == qv) {
+              sm.A[pu][pv] = n00;
+              sm.A[qu][pv] = n10;
+            } else {
+              sm.A[pu][pv] = n00;
+              sm.A[pu][qv] = n01;
+              sm.A[qu][pv] = n10;
+              sm.A[qu][qv] = n11;
+              if (u == v) sm.A[pu][qv] = sm.A[qu][pv] = 0.f;
+            }
           }
         }
-        // V <- V J: columns of pair v
-        for (int e = tid; e < K * half; e += kJacThreads) {
-          const int i = e / half, v = e - i * half;
-          const int pv = sm.p[v], qv = sm.q[v];
-          if (pv != qv) {
-            const float cv = sm.c[v], sv = sm.s[v];
-            const float x = sm.V[i][pv], y = sm.V[i][qv];
-            sm.V[i][pv] = cv * x - sv * y;
-            sm.V[i][qv] = sv * x + cv * y;
+#pragma unroll
+        for (int m = 0; m < kMaxCols; ++m) {
+          if (ci[m] >= 0) {
+            const int i = ci[m], v = cv[m];
+            const int pv = sm.p[v], qv = sm.q[v];
+            if (pv != qv) {
+              const float cvv = sm.c[v], sv = sm.s[v];
+              const float x = sm.V[i][pv], y = sm.V[i][qv];
+              sm.V[i][pv] = cvv * x - sv * y;
+              sm.V[i][qv] = sv * x + cvv * y;
+            }
           }
         }
         __syncthreads();
