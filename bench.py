@@ -18,6 +18,7 @@ JSON line.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import subprocess
@@ -52,6 +53,9 @@ def parse():
                     choices=["colour_hd", "colour_256", "hyperspectral", "nlm"],
                     help="the timed single-image workload (default: the 1920x1080 colour BLF); "
                          "nlm runs the forward only")
+    ap.add_argument("--crop", type=int, nargs=2, metavar=("H", "W"), default=None,
+                    help="time the top-left H x W crop of the workload instead (a smaller case "
+                         "for profiling; no accuracy pass and no extras)")
     ap.add_argument("--impl", default="nyf", choices=["nyf", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -65,7 +69,7 @@ CPU_SAMPLE = (192, 192)     # crop of the workload the oracle filters (and diffe
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the convolution kernels
 # on the 1920 x 1080, K = 32 workload, from the ncu captures summarised in
 # profiles/ncu_conv_kernels_colour_blf_1920x1080.md; only for the kernels as captured.
-NCU_TRAFFIC = {("conv_bwd", "fp32"): 1.420e9 + 0.253e9, ("conv_bwd", "bf16"): 1.420e9 + 0.253e9,
+NCU_TRAFFIC = {
                ("conv_combine", "fp32"): 0.323e9 + 1.035e9, ("conv_combine", "bf16"): 0.315e9 + 1.034e9,
                # both recursive-Gaussian passes (k_cols + k_rows), sigma_s 5, from
                # profiles/ncu_recursive_gaussian_colour_blf_1920x1080.md
@@ -679,6 +683,11 @@ def main():
     lib = _lib.load()
     wl = {"colour_hd": synth.colour_blf_hd, "colour_256": synth.colour_blf_small,
           "hyperspectral": synth.hyperspectral_blf, "nlm": synth.colour_nlm}[args.workload]()
+    if args.crop:
+        ch, cw = min(args.crop[0], wl.f.shape[0]), min(args.crop[1], wl.f.shape[1])
+        wl = dataclasses.replace(wl, name=f"{wl.name}_crop_{cw}x{ch}",
+                                 f=np.ascontiguousarray(wl.f[:ch, :cw]))
+        args.no_extras = True
     H, W, n = wl.f.shape
     nlm = wl.patch_radius > 0
     rho = n * (2 * wl.patch_radius + 1) ** 2 if nlm else n
@@ -787,7 +796,7 @@ def main():
     step_roof = step_roofline(counts, {k: v for k, v in zip(STAGES, stage_mean[:6 if fwdbwd else 4])
                                        if v is not None}, ms)
     accuracy = None
-    if rank == 0 and not iir:
+    if rank == 0 and not iir and not args.crop:
         try:
             blocks, errs = golden_landmarks(args.workload)
             accuracy = accuracy_blf(nyf, wl, blocks[0], args.precision, fwdbwd)
@@ -911,7 +920,7 @@ def main():
             "clocks": clk,
             "extras": extras,
         }
-        if not args.no_cpu_baseline and world == 1 and args.workload == "colour_hd":
+        if not args.no_cpu_baseline and world == 1 and args.workload == "colour_hd" and not args.crop:
             try:
                 line["cpu_baseline"] = cpu_baseline_obj(backward=fwdbwd)
             except Exception as ex:  # the oracle leg must not hide the GPU number
