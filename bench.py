@@ -69,7 +69,7 @@ CPU_SAMPLE = (192, 192)     # crop of the workload the oracle filters (and diffe
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the convolution kernels
 # on the 1920 x 1080, K = 32 workload, from the ncu captures summarised in
 # profiles/ncu_conv_kernels_colour_blf_1920x1080.md; only for the kernels as captured.
-NCU_TRAFFIC = {
+NCU_TRAFFIC = {("conv_bwd", "fp32"): 1.421e9 + 0.250e9,   # profiles/ncu_conv_bwd_colour_blf_512x1024_crop.md
                ("conv_combine", "fp32"): 0.323e9 + 1.035e9, ("conv_combine", "bf16"): 0.315e9 + 1.034e9,
                # both recursive-Gaussian passes (k_cols + k_rows), sigma_s 5, from
                # profiles/ncu_recursive_gaussian_colour_blf_1920x1080.md
