@@ -25,6 +25,16 @@ constexpr int kFbThreads = 256;
 
 __host__ __device__ inline int kpad4(int K) { return (K + 3) & ~3; }
 
+// Rows of Es / Ds (one per pixel, KB floats) are written and read as 16-byte
+// chunks; chunk c of row `row` sits at chunk position c ^ (row mod min(8, KB/4)),
+// so a warp's 16-byte stores of the same chunk of 32 consecutive rows fall in
+// distinct banks (an unswizzled row stride of KB floats puts them all in one).
+template <int KB>
+__device__ __forceinline__ int chunk_at(int row, int c) {
+  constexpr int CH = KB / 4, MASK = (CH < 8 ? CH : 8) - 1;
+  return c ^ (row & MASK);
+}
+
 template <int KB, int RB>
 __global__ void __launch_bounds__(kFbThreads, (KB <= 32 && RB != 32) ? 3 : 1)
 k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float* __restrict__ lm,
@@ -90,59 +100,71 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
     float g[KB];                                   // dPhi of this pixel
 #pragma unroll
     for (int k = 0; k < KB; ++k) g[k] = (valid && k < r) ? dphi[(int64_t)k * N + i] : 0.f;
-    // one landmark at a time: E_m, dE_m = sum_k dPhi_k W_hat[m][k], then its terms
-    for (int m = 0; m < K; ++m) {
-      const float* c = mu + m * rho;
-      float d2 = 0.f;
-      if (RB > 0) {
+    // one landmark at a time: E_m, dE_m = sum_k dPhi_k W_hat[m][k], then its terms;
+    // E goes to this thread's row of Es four landmarks at a time
+    for (int m4 = 0; m4 < K; m4 += 4) {
+      float e4[4];
 #pragma unroll
-        for (int d = 0; d < RX; ++d)
-          if (d < rho) {
-            const float t = x[d] - c[d];
+      for (int mq = 0; mq < 4; ++mq) {
+        const int m = m4 + mq;
+        e4[mq] = 0.f;
+        if (m >= K) continue;
+        const float* c = mu + m * rho;
+        float d2 = 0.f;
+        if (RB > 0) {
+#pragma unroll
+          for (int d = 0; d < RX; ++d)
+            if (d < rho) {
+              const float t = x[d] - c[d];
+              d2 = fmaf(t, t, d2);
+            }
+        } else if (RB == 0) {
+          for (int d = 0; d < rho; ++d) {
+            const float t = xs[d] - c[d];
             d2 = fmaf(t, t, d2);
           }
-      } else if (RB == 0) {
-        for (int d = 0; d < rho; ++d) {
-          const float t = xs[d] - c[d];
-          d2 = fmaf(t, t, d2);
+        } else {
+          for (int d = 0; d < rho; ++d) {
+            const float t = __ldg(p + d) - c[d];
+            d2 = fmaf(t, t, d2);
+          }
         }
-      } else {
-        for (int d = 0; d < rho; ++d) {
-          const float t = __ldg(p + d) - c[d];
-          d2 = fmaf(t, t, d2);
-        }
-      }
-      const float e = valid ? expf(-d2 * inv2s2r) : 0.f;
-      float de0 = 0.f, de1 = 0.f;
+        const float e = valid ? expf(-d2 * inv2s2r) : 0.f;
+        float de0 = 0.f, de1 = 0.f;
 #pragma unroll
-      for (int k = 0; k < KB; k += 4) {
-        if (k < r) {
-          const float4 w = *reinterpret_cast<const float4*>(Wsm + m * KP + k);
-          de0 = fmaf(g[k], w.x, de0);
-          de1 = fmaf(g[k + 1], w.y, de1);
-          de0 = fmaf(g[k + 2], w.z, de0);
-          de1 = fmaf(g[k + 3], w.w, de1);
+        for (int k = 0; k < KB; k += 4) {
+          if (k < r) {
+            const float4 w = *reinterpret_cast<const float4*>(Wsm + m * KP + k);
+            de0 = fmaf(g[k], w.x, de0);
+            de1 = fmaf(g[k + 1], w.y, de1);
+            de0 = fmaf(g[k + 2], w.z, de0);
+            de1 = fmaf(g[k + 3], w.w, de1);
+          }
         }
-      }
-      const float de = de0 + de1;
-      srp = fmaf(de * e, d2, srp);
-      const float dDm = -e * de * inv2s2r;
-      if (RB > 0) {
+        const float de = de0 + de1;
+        srp = fmaf(de * e, d2, srp);
+        const float dDm = -e * de * inv2s2r;
+        if (RB > 0) {
 #pragma unroll
-        for (int d = 0; d < RX; ++d)
-          if (d < rho) dp[d] = fmaf(dDm, 2.f * (x[d] - c[d]), dp[d]);
-      } else if (RB == 0) {
-        for (int d = 0; d < rho; ++d) ps[d] = fmaf(dDm, 2.f * (xs[d] - c[d]), ps[d]);
-      } else if (valid) {
-        float* dst = dguide + i * rho;
-        for (int d = 0; d < rho; ++d) {
-          const float v = dDm * 2.f * (__ldg(p + d) - c[d]);
-          dst[d] = (m == 0 && !add_into) ? v : dst[d] + v;
+          for (int d = 0; d < RX; ++d)
+            if (d < rho) dp[d] = fmaf(dDm, 2.f * (x[d] - c[d]), dp[d]);
+        } else if (RB == 0) {
+          for (int d = 0; d < rho; ++d) ps[d] = fmaf(dDm, 2.f * (xs[d] - c[d]), ps[d]);
+        } else if (valid) {
+          float* dst = dguide + i * rho;
+          for (int d = 0; d < rho; ++d) {
+            const float v = dDm * 2.f * (__ldg(p + d) - c[d]);
+            dst[d] = (m == 0 && !add_into) ? v : dst[d] + v;
+          }
         }
+        e4[mq] = e;
       }
-      Es[tid * KB + m] = e;
+      *reinterpret_cast<float4*>(Es + tid * KB + 4 * chunk_at<KB>(tid, m4 >> 2)) =
+          make_float4(e4[0], e4[1], e4[2], e4[3]);
     }
-    for (int m = K; m < KB; ++m) Es[tid * KB + m] = 0.f;
+    for (int c4 = (K + 3) >> 2; c4 < KB / 4; ++c4)
+      *reinterpret_cast<float4*>(Es + tid * KB + 4 * chunk_at<KB>(tid, c4)) =
+          make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) {
       float* dst = dguide + i * rho;
       if (RB > 0) {
@@ -154,14 +176,16 @@ k_features_bwd(const float* __restrict__ guide, int64_t N, int rho, const float*
       }
     }
 #pragma unroll
-    for (int k = 0; k < KB; ++k) Ds[tid * KB + k] = g[k];
+    for (int c4 = 0; c4 < KB / 4; ++c4)
+      *reinterpret_cast<float4*>(Ds + tid * KB + 4 * chunk_at<KB>(tid, c4)) =
+          make_float4(g[4 * c4], g[4 * c4 + 1], g[4 * c4 + 2], g[4 * c4 + 3]);
     __syncthreads();
     // G_W += E^T dPhi over this round's pixels: two 16-byte loads per 16 FMAs
     if (own) {
 #pragma unroll 4
       for (int px = grp; px < kFbThreads; px += G) {
-        const float4 ev = *reinterpret_cast<const float4*>(Es + px * KB + m0);
-        const float4 dv = *reinterpret_cast<const float4*>(Ds + px * KB + k0);
+        const float4 ev = *reinterpret_cast<const float4*>(Es + px * KB + 4 * chunk_at<KB>(px, m0 >> 2));
+        const float4 dv = *reinterpret_cast<const float4*>(Ds + px * KB + 4 * chunk_at<KB>(px, k0 >> 2));
         const float e4[4] = {ev.x, ev.y, ev.z, ev.w}, d4[4] = {dv.x, dv.y, dv.z, dv.w};
 #pragma unroll
         for (int a = 0; a < 4; ++a)
