@@ -17,6 +17,10 @@
 // The box window (the NLM search window) runs as running sums over the true
 // radius instead: the first output of a row or column segment sums 2S+1 inputs,
 // each next one adds the entering input and subtracts the leaving one.
+//
+// Per mode k the CTA runs two phases separated by barriers: the vertical pass of
+// every quantity pair (one output buffer per pair), then, while phi_{k+1}
+// streams into the phi plane, the horizontal pass and combine of every pair.
 #pragma once
 
 #include "nyf_internal.cuh"
@@ -53,7 +57,7 @@ constexpr int kMaxTapRadius = NYF_MAX_S;   // tap arrays in launch parameters co
 // pass gives each thread RV rows of one halo column, the horizontal pass RH
 // columns of one output row; NQ quantities per CTA, processed in pairs with
 // packed FP32x2 FMAs (one instruction, two planes).  Shared memory: NQ image
-// planes, two phi planes (double buffer) and the vertical-pass plane pair.
+// planes, the phi plane and one vertical-pass plane pair per quantity pair.
 template <int S, bool WIDE = true>
 struct ConvCfg {
   static constexpr int TH = 32;
@@ -65,9 +69,11 @@ struct ConvCfg {
   static constexpr int HW = TW + 2 * S;
   static constexpr int PS = HW | 1;           // odd row stride: conflict-free column/row walks
   static constexpr int PLANE = HH * PS;
-  static constexpr size_t smem = sizeof(float) * ((size_t)(NQ + 2) * PLANE + (size_t)2 * TH * PS);
+  // shared memory: NQ image planes, phi_k, and the vertical pass of every quantity pair
+  static constexpr size_t smem =
+      sizeof(float) * ((size_t)(NQ + 1) * PLANE + (size_t)(NQ / 2) * 2 * TH * PS);
   static_assert(TH * (TW / RH) == kConvThreads, "one horizontal task per thread");
-  static_assert((TH / RV) * HW <= kConvThreads, "at most one vertical task per thread");
+  static_assert((TH / RV) * HW <= kConvThreads, "at most one vertical task per thread and pair");
   static_assert(smem <= 227 * 1024, "shared memory budget");
 };
 
@@ -149,8 +155,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
   constexpr int NP = NQ / 2;        // quantity pairs per CTA
   extern __shared__ float sm[];
   float* F = sm;                    // NQ image planes (tile + halo)
-  float* PB = F + NQ * PLANE;       // two phi planes (tile + halo)
-  float2* M = reinterpret_cast<float2*>(PB + 2 * PLANE);   // vertical pass, TH x HW pairs
+  float* P = F + NQ * PLANE;        // phi_k (tile + halo)
+  float2* M = reinterpret_cast<float2*>(P + PLANE);   // NP vertical passes, TH x PS pairs each
   const int tid = threadIdx.x;
   const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
   const int q0 = blockIdx.z * NQ;
@@ -169,7 +175,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
     const bool in = c < n && gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
     cp_async4(F + qi * PLANE + yy * PS + xx, in ? a.f + ((int64_t)gy * a.W + gx) * n + c : a.f, in);
   }
-  if (kb < r) stage_phi<S, WIDE>(a, PB, kb, ty0, tx0);
+  if (kb < r) stage_phi<S, WIDE>(a, P, kb, ty0, tx0);
   cp_async_commit();
 
   const float2* g = a.taps + (kMaxTapRadius - S);   // (g, g) pairs, from the constant bank
@@ -182,69 +188,74 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
 
   const int hy = tid / (TW / RH), hx0 = (tid % (TW / RH)) * RH;
   const int vx = tid % HW, vy0 = (tid / HW) * RV;
-  const bool vactive = tid < (TH / RV) * HW;     // one vertical task per thread (or none)
+  const bool vactive = tid < (TH / RV) * HW;     // one vertical task per thread and pair (or none)
 
   for (int k = kb; k < r; ++k) {
-    // Prefetch phi_{k+1} into the other buffer while phi_k is consumed.  The
-    // buffer was last read in iteration k-1, which ended with a barrier.
-    if (k + 1 < r) {
-      stage_phi<S, WIDE>(a, PB + ((k + 1 - kb) & 1) * PLANE, k + 1, ty0, tx0);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const float* P = PB + ((k - kb) & 1) * PLANE;
+    cp_async_wait<0>();
+    __syncthreads();                 // phi_k (and the image planes) landed; M is free
+    float pc[RH];                    // phi_k at this thread's output pixels
+#pragma unroll
+    for (int j = 0; j < RH; ++j) pc[j] = P[(hy + S) * PS + hx0 + j + S];
+    // vertical pass of every quantity pair
 #pragma unroll
     for (int pi = 0; pi < NP; ++pi) {
       const int qa = q0 + 2 * pi, qb = qa + 1;
-      if (qa <= n) {                             // uniform over the block
+      if (qa <= n && vactive) {      // qa uniform over the block
         // pair member x: image channel qa (or 1 if qa == n); member y: channel
         // qb (1 if qb == n, 0 if qb > n)
         const float* Fa = F + (2 * pi) * PLANE;
         const float* Fb = Fa + PLANE;
         const bool a_den = qa == n, b_den = qb == n, b_none = qb > n;
-        if (vactive) {
-          float2 va[RV];
-          auto vin = [&](int i) {     // (phi f_qa, phi f_qb) at halo row vy0 + i of column vx
-            const int off = (vy0 + i) * PS + vx;
-            const float p = P[off];
-            return f2(a_den ? p : p * Fa[off], b_den ? p : (b_none ? 0.f : p * Fb[off]));
-          };
-          if (a.box) {
-            // box window: running sums over the true radius (2 operations per output
-            // after the first; the halo is that of the compiled radius S)
-            const int lo = S - a.S_true, T1 = 2 * a.S_true + 1;
-            float2 run = f2(0.f, 0.f);
-            for (int i = lo; i < lo + T1; ++i) run = __ffma2_rn(f2(1.f, 1.f), vin(i), run);
-            va[0] = run;
+        float2 va[RV];
+        auto vin = [&](int i) {     // (phi f_qa, phi f_qb) at halo row vy0 + i of column vx
+          const int off = (vy0 + i) * PS + vx;
+          const float p = P[off];
+          return f2(a_den ? p : p * Fa[off], b_den ? p : (b_none ? 0.f : p * Fb[off]));
+        };
+        if (a.box) {
+          // box window: running sums over the true radius (2 operations per output
+          // after the first; the halo is that of the compiled radius S)
+          const int lo = S - a.S_true, T1 = 2 * a.S_true + 1;
+          float2 run = f2(0.f, 0.f);
+          for (int i = lo; i < lo + T1; ++i) run = __ffma2_rn(f2(1.f, 1.f), vin(i), run);
+          va[0] = run;
 #pragma unroll
-            for (int j = 1; j < RV; ++j) {
-              run = __ffma2_rn(f2(1.f, 1.f), vin(j + lo + T1 - 1), run);
-              run = __ffma2_rn(f2(-1.f, -1.f), vin(j - 1 + lo), run);
-              va[j] = run;
-            }
-          } else {
+          for (int j = 1; j < RV; ++j) {
+            run = __ffma2_rn(f2(1.f, 1.f), vin(j + lo + T1 - 1), run);
+            run = __ffma2_rn(f2(-1.f, -1.f), vin(j - 1 + lo), run);
+            va[j] = run;
+          }
+        } else {
 #pragma unroll
-            for (int j = 0; j < RV; ++j) va[j] = f2(0.f, 0.f);
+          for (int j = 0; j < RV; ++j) va[j] = f2(0.f, 0.f);
 #pragma unroll
-            for (int i = 0; i < RV + 2 * S; ++i) {
-              const float2 v = vin(i);
+          for (int i = 0; i < RV + 2 * S; ++i) {
+            const float2 v = vin(i);
 #pragma unroll
-              for (int j = 0; j < RV; ++j) {
-                const int t = i - j;
-                if (t >= 0 && t < T) va[j] = __ffma2_rn(g[t], v, va[j]);
-              }
+            for (int j = 0; j < RV; ++j) {
+              const int t = i - j;
+              if (t >= 0 && t < T) va[j] = __ffma2_rn(g[t], v, va[j]);
             }
           }
-#pragma unroll
-          for (int j = 0; j < RV; ++j) M[(vy0 + j) * PS + vx] = va[j];
         }
-        __syncthreads();
+        float2* Mp = M + pi * (TH * PS);
+#pragma unroll
+        for (int j = 0; j < RV; ++j) Mp[(vy0 + j) * PS + vx] = va[j];
+      }
+    }
+    __syncthreads();                 // M complete; nobody reads P beyond this point
+    if (k + 1 < r) {                 // phi_{k+1} streams in under the horizontal pass
+      stage_phi<S, WIDE>(a, P, k + 1, ty0, tx0);
+      cp_async_commit();
+    }
+#pragma unroll
+    for (int pi = 0; pi < NP; ++pi) {
+      const int qa = q0 + 2 * pi, qb = qa + 1;
+      if (qa <= n) {                 // uniform over the block
+        const bool b_none = qb > n;
+        const float2* mr = M + pi * (TH * PS) + hy * PS + hx0;
         float2 hb[RH];
-        if (a.box) {                             // running sums along the row
-          const float2* mr = M + hy * PS + hx0;
+        if (a.box) {                 // running sums along the row
           const int lo = S - a.S_true, T1 = 2 * a.S_true + 1;
           float2 run = f2(0.f, 0.f);
           for (int i = lo; i < lo + T1; ++i) run = __ffma2_rn(f2(1.f, 1.f), mr[i], run);
@@ -260,7 +271,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
           for (int j = 0; j < RH; ++j) hb[j] = f2(0.f, 0.f);
 #pragma unroll
           for (int i = 0; i < RH + 2 * S; ++i) {
-            const float2 v = M[hy * PS + hx0 + i];
+            const float2 v = mr[i];
 #pragma unroll
             for (int j = 0; j < RH; ++j) {
               const int t = i - j;
@@ -269,15 +280,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_combine(const __grid_c
           }
         }
 #pragma unroll
-        for (int j = 0; j < RH; ++j) {
-          const float p = P[(hy + S) * PS + hx0 + j + S];
-          acc[pi][j] = __ffma2_rn(f2(p, p), hb[j], acc[pi][j]);
-        }
+        for (int j = 0; j < RH; ++j) acc[pi][j] = __ffma2_rn(f2(pc[j], pc[j]), hb[j], acc[pi][j]);
         if (a.cout && ty0 + hy < a.H) {          // keep C_kq for the backward pass
           float* ca = a.cout + ((int64_t)(k - kb) * (n + 1) + qa) * a.N + (int64_t)(ty0 + hy) * a.W + tx0 + hx0;
           store_pair_row<RH>(ca, b_none ? nullptr : ca + a.N, hb, a.W - (tx0 + hx0));
         }
-        __syncthreads();
       }
     }
   }

@@ -15,7 +15,9 @@
 //   k_gram_reduce   FP64 sum of the partials, the covariance and the mean;
 //   k_eig_pca       one CTA: Householder tridiagonalisation, bisection for every
 //                   eigenvalue and inverse iteration for the q leading
-//                   eigenvectors, in FP32 (shared memory);
+//                   eigenvectors (all q at once, a warp per vector, with
+//                   Gram-Schmidt inside clusters of close eigenvalues), in FP32
+//                   (shared memory);
 //   k_orthonormalize the q columns re-orthonormalised in FP64;
 //   k_pca_project   p~(x) for every pixel (16 x 16 tiles, one thread per pixel).
 #include <math.h>
@@ -210,11 +212,60 @@ __device__ int sturm_count(const float* d, const float* e2, int n, float x, floa
   int c = 0;
   float q = 1.f;
   for (int k = 0; k < n; ++k) {
-    q = (d[k] - x) - (k > 0 ? e2[k - 1] / q : 0.f);
+    q = (d[k] - x) - (k > 0 ? __fdividef(e2[k - 1], q) : 0.f);   // |q| >= pivmin, a normal number
     if (fabsf(q) < pivmin) q = -pivmin;
     c += q < 0.f;
   }
   return c;
+}
+
+// Solves (T - shift I) y = x in place for the symmetric tridiagonal T (diagonal
+// d, off-diagonal e, n rows) by Gaussian elimination with partial pivoting, one
+// thread.  The row being eliminated is carried in registers (diagonal a,
+// superdiagonal b; its next entry is always zero), so each step's dependency
+// chain is a few arithmetic operations; U (pivot, first and second
+// superdiagonal) goes to ua, u1, u2.  Zero pivots are replaced by `tiny`.
+__device__ void tri_solve(const float* d, const float* e, int n, float shift, float tiny,
+                          float* x, float* ua, float* u1, float* u2) {
+  float a = d[0] - shift, b = n > 1 ? e[0] : 0.f;
+  float xk = x[0];
+  for (int k = 0; k < n - 1; ++k) {
+    const float sub = e[k];
+    const float an = d[k + 1] - shift;
+    const float bn = k + 1 < n - 1 ? e[k + 1] : 0.f;
+    const float xn = x[k + 1];
+    if (fabsf(a) >= fabsf(sub)) {            // pivot: the carried row
+      if (a == 0.f) a = tiny;
+      const float m = __fdividef(sub, a);    // |m| <= 1, a normal
+      ua[k] = a;
+      u1[k] = b;
+      u2[k] = 0.f;
+      x[k] = xk;
+      a = an - m * b;
+      b = bn;
+      xk = xn - m * xk;
+    } else {                                 // pivot: the next row (|sub| > |a|)
+      const float m = __fdividef(a, sub);
+      ua[k] = sub;
+      u1[k] = an;
+      u2[k] = bn;
+      x[k] = xn;
+      a = b - m * an;
+      b = -m * bn;
+      xk = xk - m * xn;
+    }
+  }
+  ua[n - 1] = a != 0.f ? a : tiny;
+  u1[n - 1] = 0.f;
+  u2[n - 1] = 0.f;
+  x[n - 1] = xk;
+  float x1 = 0.f, x2 = 0.f;                  // x[k + 1], x[k + 2]
+  for (int k = n - 1; k >= 0; --k) {
+    const float s = (x[k] - u1[k] * x1 - u2[k] * x2) / ua[k];
+    x[k] = s;
+    x2 = x1;
+    x1 = s;
+  }
 }
 
 __global__ void __launch_bounds__(kJacobiThreads) k_eig_pca(const float* __restrict__ C, int rho, int q,
@@ -231,11 +282,9 @@ __global__ void __launch_bounds__(kJacobiThreads) k_eig_pca(const float* __restr
   float* lam = beta + n;                         // ascending
   float* vv = lam + n;                           // reflector / work vector
   float* pw = vv + n;                            // p, then w
-  float* ga = pw + n;                            // elimination: pivots
-  float* gu1 = ga + n;                           //   first superdiagonal
-  float* gu2 = gu1 + n;                          //   second superdiagonal
-  float* gx = gu2 + n;                           //   right-hand side / solution
+  float* gwork = pw + n;                         // per warp: U factors of its solves (3 n)
   __shared__ float red[kJacobiThreads / 32];
+  __shared__ float coef[32];                     // Gram-Schmidt coefficients (q <= 32)
   __shared__ float bounds[3];                    // lo, hi, ||T||
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
   (void)state;                                   // fixed trip counts: no status to latch
@@ -320,71 +369,54 @@ __global__ void __launch_bounds__(kJacobiThreads) k_eig_pca(const float* __restr
     lam[i] = 0.5f * (a + b);
   }
   __syncthreads();
-  // ---- 3. inverse iteration for the q largest, warp 0 (lane 0 solves)
-  if (warp == 0) {
+  // ---- 3. inverse iteration for the q largest eigenvalues, all vectors at once: each
+  // iteration solves (T - lam_j I) y_j = x_j for every j (a warp per vector, its lane 0
+  // solving), then, in order of j, orthogonalises y_j against the y_i (i < j) whose
+  // eigenvalues lie within ortol of lam_j (classical Gram-Schmidt) and normalises it
+  {
     const float tiny = eps * tnorm, ortol = 1e-3f * tnorm;
-    for (int j = 0; j < q; ++j) {
-      const float lj = lam[n - 1 - j];
-      for (int i = lane; i < n; i += 32) gx[i] = (float)((37 * (i + 1) + 11 * j) % 97) / 97.f - 0.5f;
-      __syncwarp();
-      for (int it = 0; it < kInvIters; ++it) {
-        if (lane == 0) {                         // (T - lj I) y = gx, partial pivoting
-          for (int k = 0; k < n; ++k) {
-            ga[k] = d[k] - lj;
-            gu1[k] = k < n - 1 ? e[k] : 0.f;
-            gu2[k] = 0.f;
-          }
-          for (int k = 0; k < n - 1; ++k) {
-            const float sub = e[k];
-            if (fabsf(ga[k]) >= fabsf(sub)) {
-              if (ga[k] == 0.f) ga[k] = tiny;
-              const float m = sub / ga[k];
-              ga[k + 1] -= m * gu1[k];
-              gx[k + 1] -= m * gx[k];
-            } else {
-              const float m = ga[k] / sub;
-              const float uk = gu1[k];
-              const float u1n = ga[k + 1];
-              const float u2n = k + 1 < n - 1 ? gu1[k + 1] : 0.f;
-              ga[k] = sub;
-              ga[k + 1] = uk - m * u1n;
-              gu1[k] = u1n;
-              gu2[k] = u2n;
-              if (k + 1 < n - 1) gu1[k + 1] = -m * u2n;
-              const float xk = gx[k];
-              gx[k] = gx[k + 1];
-              gx[k + 1] = xk - m * gx[k + 1];
+    float* wa = gwork + warp * 3 * n;            // this warp's U factors
+    for (int e3 = tid; e3 < q * n; e3 += blockDim.x) {
+      const int j = e3 / n, i = e3 - j * n;
+      X[e3] = (float)((37 * (i + 1) + 11 * j) % 97) / 97.f - 0.5f;
+    }
+    __syncthreads();
+    for (int it = 0; it < kInvIters; ++it) {
+      for (int j = warp; j < q; j += nwarp)
+        if (lane == 0) tri_solve(d, e, n, lam[n - 1 - j], tiny, X + j * n, wa, wa + n, wa + 2 * n);
+      __syncthreads();
+      for (int j = 0; j < q; ++j) {
+        float* xj = X + j * n;
+        const float lj = lam[n - 1 - j];
+        bool any = false;                          // uniform: an earlier vector of its cluster
+        for (int i2 = 0; i2 < j; ++i2) any |= fabsf(lam[n - 1 - i2] - lj) < ortol;
+        if (any) {
+          for (int i2 = warp; i2 < j; i2 += nwarp) {
+            float dt = 0.f;
+            if (fabsf(lam[n - 1 - i2] - lj) < ortol) {
+              const float* xi = X + i2 * n;
+              for (int i = lane; i < n; i += 32) dt = fmaf(xi[i], xj[i], dt);
+              for (int o = 16; o > 0; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
             }
+            if (lane == 0) coef[i2] = dt;
           }
-          for (int k = n - 1; k >= 0; --k) {
-            float s = gx[k];
-            if (k + 1 < n) s -= gu1[k] * gx[k + 1];
-            if (k + 2 < n) s -= gu2[k] * gx[k + 2];
-            gx[k] = s / (ga[k] != 0.f ? ga[k] : tiny);
+          __syncthreads();
+          for (int c = tid; c < n; c += blockDim.x) {
+            float v = xj[c];
+            for (int i2 = 0; i2 < j; ++i2) v = fmaf(-coef[i2], X[i2 * n + c], v);
+            xj[c] = v;
           }
-        }
-        __syncwarp();
-        for (int i2 = 0; i2 < j; ++i2) {         // reorthogonalise inside the cluster
-          if (!(fabsf(lam[n - 1 - i2] - lj) < ortol)) continue;
-          const float* xi = X + i2 * n;
-          float dt = 0.f;
-          for (int i = lane; i < n; i += 32) dt += xi[i] * gx[i];
-          for (int o = 16; o > 0; o >>= 1) dt += __shfl_xor_sync(0xffffffffu, dt, o);
-          for (int i = lane; i < n; i += 32) gx[i] -= dt * xi[i];
-          __syncwarp();
+          __syncthreads();
         }
         float nn = 0.f;
-        for (int i = lane; i < n; i += 32) nn += gx[i] * gx[i];
-        for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        for (int c = tid; c < n; c += blockDim.x) nn = fmaf(xj[c], xj[c], nn);
+        nn = block_sum_f(nn, red, tid);
         const float inv = nn > 0.f ? rsqrtf(nn) : 0.f;
-        for (int i = lane; i < n; i += 32) gx[i] *= inv;
-        __syncwarp();
+        for (int c = tid; c < n; c += blockDim.x) xj[c] *= inv;
+        __syncthreads();
       }
-      for (int i = lane; i < n; i += 32) X[j * n + i] = gx[i];
-      __syncwarp();
     }
   }
-  __syncthreads();
   // ---- 4. u_j = H_0 H_1 ... H_{n-3} x_j, a warp per vector
   for (int j = warp; j < q; j += nwarp) {
     float* x = X + j * n;
@@ -527,7 +559,8 @@ size_t pca_scratch_bytes(int n, int r) {
 
 size_t pca_jacobi_smem(int rho) {
   const int ld = rho | 1;
-  return sizeof(float) * ((size_t)rho * ld + (size_t)rho * 32 + 11 * (size_t)rho);
+  return sizeof(float) * ((size_t)rho * ld + (size_t)rho * 32 + 9 * (size_t)rho +
+                          3 * (size_t)rho * (kJacobiThreads / 32));
 }
 
 cudaError_t launch_patch_pca(const float* f, int H, int W, int n, int r, int q, void* scratch,
