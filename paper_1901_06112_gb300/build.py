@@ -12,7 +12,7 @@ INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnyf.so")
 
-SOURCES = ["api.cu", "kmeans.cu", "kmeans_tc.cu", "eig.cu", "features_tc.cu", "conv.cu", "conv_a.cu", "conv_b.cu",
+SOURCES = ["api.cu", "kmeans.cu", "kmeans_tc.cu", "eig.cu", "features.cu", "features_tc.cu", "conv.cu", "conv_a.cu", "conv_b.cu",
            "conv_c.cu", "backward.cu", "backward_a.cu", "backward_b.cu", "backward_c.cu",
            "noalloc.cu", "conv_tc.cu", "umma_selftest.cu", "iir.cu", "iir_cols_a.cu",
            "iir_cols_b.cu", "iir_rows_a.cu", "iir_rows_b.cu", "pca.cu"]

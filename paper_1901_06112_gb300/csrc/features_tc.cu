@@ -1,7 +1,6 @@
 // Per-pixel Nystrom features on the fifth-generation tensor cores (tcgen05),
-// for every guide (colour pixels, hyperspectral pixels, NLM patches, PCA
-// coordinates; the guide dimension is padded to a multiple of 16 with zeros):
-// Eqs. (11)-(12) as two contractions,
+// for guides of dimension rho >= 16 (hyperspectral pixels, NLM patches, PCA
+// coordinates): Eqs. (11)-(12) as two contractions,
 //   X   = P~ M~^T              (N x rho . rho x K: the cross term of the distances)
 //   D   = ||p~||^2 + ||mu~||^2 - 2 X,   E = exp(-D / (2 sigma_r^2))   (Eq. (11))
 //   Phi = E W_hat               (N x K . K x K, Eq. (12) with the symmetric factor)
@@ -357,14 +356,14 @@ cudaError_t ft_launch(const FtArgs& a, int tile_floats, int64_t ntiles, cudaStre
 
 }  // namespace
 
-size_t features_nlm_smem_bytes(int K, int n, int r) {
-  const int rho = (2 * r + 1) * (2 * r + 1) * n;
-  return (size_t)ft_layout(rho, K, (kNlmTY + 2 * r) * (kNlmTX + 2 * r) * n).total;
+size_t features_tc_smem_bytes(int rho, int K, int n, int r) {
+  const int tile = r > 0 ? (kNlmTY + 2 * r) * (kNlmTX + 2 * r) * n : 0;
+  return (size_t)ft_layout(rho, K, tile).total;
 }
 
-cudaError_t launch_features(const float* guide, int64_t N, int rho, const float* landmarks, int K,
-                            float sigma_r, const float* what, const DevState* state, void* phi,
-                            bool bf16, cudaStream_t st) {
+cudaError_t launch_features_tc(const float* guide, int64_t N, int rho, const float* landmarks,
+                               int K, float sigma_r, const float* what, const DevState* state,
+                               void* phi, bool bf16, cudaStream_t st) {
   FtArgs a{};
   a.guide = guide;
   a.N = N;
@@ -380,9 +379,9 @@ cudaError_t launch_features(const float* guide, int64_t N, int rho, const float*
   return ft_launch<false>(a, 0, (N + kFtRows - 1) / kFtRows, st);
 }
 
-cudaError_t launch_features_nlm(const float* f, int H, int W, int n, int r, const float* landmarks,
-                                int K, float sigma_r, const float* what, const DevState* state,
-                                void* phi, bool bf16, cudaStream_t st) {
+cudaError_t launch_features_nlm_tc(const float* f, int H, int W, int n, int r,
+                                   const float* landmarks, int K, float sigma_r, const float* what,
+                                   const DevState* state, void* phi, bool bf16, cudaStream_t st) {
   FtArgs a{};
   a.f = f;
   a.H = H;

@@ -130,7 +130,6 @@ cudaError_t launch_kmeans_batched(const KmItem* items, int count, int rho, int K
                                   cudaStream_t st);
 cudaError_t launch_eig_batched(const EigItem* items, int count, int K, int rho, double tau,
                                cudaStream_t st);
-// Features on the tensor cores (features_tc.cu), every guide dimension.
 cudaError_t launch_features(const float* guide, int64_t N, int rho, const float* landmarks, int K,
                             float sigma_r, const float* what, const DevState* state, void* phi,
                             bool bf16, cudaStream_t st);
@@ -138,6 +137,15 @@ cudaError_t launch_features_nlm(const float* f, int H, int W, int n, int r, cons
                                 int K, float sigma_r, const float* what, const DevState* state,
                                 void* phi, bool bf16, cudaStream_t st);
 size_t features_nlm_smem_bytes(int K, int n, int r);
+// Tensor-core (tcgen05) features for guides of dimension rho >= kFeaturesTcMinRho.
+constexpr int kFeaturesTcMinRho = 16;
+cudaError_t launch_features_tc(const float* guide, int64_t N, int rho, const float* landmarks,
+                               int K, float sigma_r, const float* what, const DevState* state,
+                               void* phi, bool bf16, cudaStream_t st);
+cudaError_t launch_features_nlm_tc(const float* f, int H, int W, int n, int r,
+                                   const float* landmarks, int K, float sigma_r, const float* what,
+                                   const DevState* state, void* phi, bool bf16, cudaStream_t st);
+size_t features_tc_smem_bytes(int rho, int K, int n, int r);
 cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void* phi, bool bf16,
                                 int tile, int spatial, float sigma_s, int S, DevState* state,
                                 float* out, float* eta_out, float* zeta_ws, float* cout,
