@@ -20,8 +20,15 @@
 namespace nyf {
 namespace {
 
-constexpr int kFbBlocks = 456;      // features-backward CTAs (3 per SM)
 constexpr int kFbThreads = 256;
+constexpr int kFbBlocks = 456;      // features-backward CTAs (3 per SM), at most
+// CTAs of the features backward for N pixels: one round of kFbThreads pixels per CTA
+// at least (a small image does not pay for 456 partials); fixed by N, so every sum
+// keeps its order for a given image size
+inline int fb_blocks(int64_t N) {
+  const int64_t b = (N + kFbThreads - 1) / kFbThreads;
+  return (int)(b < 1 ? 1 : (b < kFbBlocks ? b : kFbBlocks));
+}
 
 __host__ __device__ inline int kpad4(int K) { return (K + 3) & ~3; }
 
@@ -367,7 +374,7 @@ cudaError_t fb_launch(const float* guide, int64_t N, int rho, const float* lm, i
   cudaError_t e = cudaFuncSetAttribute(k_features_bwd<KB, RB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_features_bwd<KB, RB><<<kFbBlocks, kFbThreads, smem, st>>>(guide, N, rho, lm, K, inv2s2r, what,
+  k_features_bwd<KB, RB><<<fb_blocks(N), kFbThreads, smem, st>>>(guide, N, rho, lm, K, inv2s2r, what,
                                                              state, dphi, dguide, add_into,
                                                              gw_part, sr_part);
   count_launches(1);
@@ -498,10 +505,10 @@ cudaError_t launch_bwd_features(const float* f, const float* guide, int H, int W
   else if (K <= 32) e = fb_rb<32>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);
   else e = fb_rb<64>(guide, N, rho, landmarks, K, inv2s2r, what, state, dphi, dguide, add_into, gw_part, sr_part, st);
   if (e != cudaSuccess) return e;
-  k_gw_reduce<<<K, 256, 0, st>>>(gw_part, kFbBlocks, K, Z, gw, rowdot);
+  k_gw_reduce<<<K, 256, 0, st>>>(gw_part, fb_blocks(N), K, Z, gw, rowdot);
   count_launches(1);
   const int64_t n_ss = bwd_ctas(Sc, H, W, n);
-  k_bwd_tail<<<1, 256, 0, st>>>(K, sigma_r, rowdot, sr_part, kFbBlocks, spart, n_ss, state,
+  k_bwd_tail<<<1, 256, 0, st>>>(K, sigma_r, rowdot, sr_part, fb_blocks(N), spart, n_ss, state,
                                 grad_sigma);
   count_launches(1);
   return cudaGetLastError();
