@@ -338,10 +338,16 @@ nyf_status nyf_selftest_wait_timeout(int limit, int* status, void* stream);
  * items[b].offset of the packed buffers f / out / grad_out / grad_f (device);
  * items is a host array read during the call.  Each image uses its own
  * sigma_s, sigma_r (and conv_tile unless NYF_TILE_AUTO) and the shared
- * fields of *params; landmarks come from k-means per image.  The images are
- * spread over a small pool of internal streams of the current device, forked
+ * fields of *params; landmarks come from k-means per image.  The steps that
+ * are small per image run as one launch per step for the whole batch, on
+ * `stream`: the k-means of every image (when its rows take the CUDA-core
+ * assignment pass, i.e. n outside 16..80, and params->sample_frac >= 1) or
+ * the copies of given landmarks, then the eigendecompositions.  The rest
+ * (features, convolutions, and the k-means of the other cases) runs per
+ * image on a small pool of internal streams of the current device, forked
  * from and joined back to `stream` with events, so the whole call can be
- * captured into a CUDA graph and replayed.  The pool (streams and events) is
+ * captured into a CUDA graph and replayed.  Every image's result is bitwise
+ * that of the per-image call with the same arguments.  The pool (streams and events) is
  * created by the first batched call made on a device, so make that first call
  * outside any stream capture (stream creation is not allowed while a capture
  * is in progress).  Do not issue batched calls on the same device from several

@@ -460,11 +460,7 @@ cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spat
     }
     a.tg[t] = make_float2(g, g);
     a.td[t] = make_float2(gd, gd);
-    a.taps[kMaxTapRadius + t] = a.taps[kMaxTapRadius - t] = make_float2(g, gd);
   }
-  a.inv2s2 = a.box ? 0.f : (float)(1.0 / (2.0 * (double)sigma_s * sigma_s));
-  a.inv_s3 = a.box ? 0.f : (float)(1.0 / ((double)sigma_s * sigma_s * sigma_s));
-  a.S_true = S;
   a.k_begin = k_begin;
   a.k_end = k_end;
   a.accumulate = first ? 0 : 1;

@@ -53,9 +53,6 @@ struct BwdArgs {
   int atomic_dphi;        // quantities split over several CTAs: accumulate dphi atomically
   float* df;              // N x n, direct image term
   float* sig_part;        // one sigma_s partial per CTA
-  float inv2s2, inv_s3;
-  int S_true;
-  float2 taps[2 * kMaxTapRadius + 1];
   // (g(t), g(t)) and (g'(t), g'(t)) for t = 0..S_compiled, zero beyond the true radius
   float2 tg[kMaxTapRadius + 1];
   float2 td[kMaxTapRadius + 1];

@@ -261,3 +261,34 @@ def test_autotuner_picks_a_valid_variant(nyf, tmp_path, monkeypatch):
     assert best[21] == "wide"
     assert (tmp_path / "tune.json").exists()
     print(f"[parity] autotuned variants: {best}")
+
+
+def test_deep_guide_batch_equals_per_image_calls(nyf):
+    # n = 20 channels: k-means rows of dimension 20 take the tensor-core assignment pass, so
+    # the batch runs per image on the stream pool; with landmarks given, the landmark
+    # copies and the eigendecompositions run as stage-batched launches.  Both are bitwise
+    # the per-image calls.
+    shapes = [(40, 56), (23, 70), (64, 33)]
+    ss, sr = [1.5, 2.5, 1.0], [0.4, 0.6, 0.5]
+    r = np.random.default_rng(11)
+    imgs = [r.uniform(0, 1, size=(H, W, 20)).astype(np.float32) for H, W in shapes]
+    P = nyf.Params(K=8, kmeans_iters=3, seed=5)
+    bt = nyf.Batched(shapes, ss, sr, P, n=20)
+    f = bt.pack(imgs)
+    lm = torch.from_numpy(np.stack([im.reshape(-1, 20)[:: 97][:8] for im in imgs])).cuda().contiguous()
+    for landmarks in (None, lm):
+        out = bt.forward(f, landmarks=landmarks)
+        G = torch.randn(f.shape, generator=torch.Generator().manual_seed(2)).cuda()
+        gf, gs = bt.backward(f, out, G)
+        torch.cuda.synchronize()
+        for b, (H, W) in enumerate(shapes):
+            Pb = nyf.Params(sigma_s=ss[b], sigma_r=sr[b], K=8, kmeans_iters=3, seed=5,
+                            save_for_backward=True)
+            fb = torch.from_numpy(imgs[b]).cuda()
+            ws = nyf.make_workspace(H, W, 20, 20, Pb)
+            ob = nyf.blf(fb, Pb, ws=ws, landmarks=None if landmarks is None else landmarks[b])
+            bb = nyf.blf_backward(fb, Pb, ob, bt.unpack(G)[b].contiguous(), ws)
+            assert torch.equal(bt.unpack(out)[b], ob), (b, landmarks is None)
+            assert torch.equal(bt.unpack(gf)[b], bb.grad_f), (b, landmarks is None)
+            assert torch.equal(gs[b], bb.grad_sigma), (b, landmarks is None)
+            assert bt.stats(b)["status"] == 0
