@@ -44,7 +44,7 @@ WsLayout ws_layout(const WsShape& s) {
   // backward only: dL/dphi, reduction partials, G_W / Z / row dots, the adjoint
   // planes a_q and the forward's convolved planes C_kq
   const size_t nq1 = (size_t)s.n + 1;
-  L.dphi = take(s.bwd ? sizeof(float) * K * N : 0);
+  L.dphi = take(s.bwd ? sizeof(float) * K * N * (size_t)(s.dphi_slices > 1 ? s.dphi_slices : 1) : 0);
   L.gpart = take(s.bwd ? sizeof(float) * backward_gpart_floats(s.K) : 0);
   L.spart = take(s.bwd ? sizeof(float) * backward_spart_floats(s.H, s.W, s.n) : 0);
   L.gw = take(s.bwd ? sizeof(double) * (3 * K * K + K) : 0);   // G_W, Z, row dots, A o D2
@@ -181,6 +181,8 @@ WsShape shape_for(int H, int W, int n, int rho, const nyf_params* p) {
   s.bwd = p->save_for_backward != NYF_SAVE_NONE && p->patch_radius == 0;
   s.recompute = p->save_for_backward == NYF_SAVE_RECOMPUTE;
   s.iir = p->spatial == NYF_GAUSSIAN_IIR;
+  const int Sc = conv_compiled_radius(window_radius(p));
+  s.dphi_slices = (s.bwd && Sc > 0) ? bwd_dphi_slices(Sc, n) : 1;
   return s;
 }
 

@@ -349,6 +349,22 @@ k_bwd_tail(int K, float sigma_r, const double* __restrict__ rowdot,
 }
 
 // dL/d zeta_q as planes: a_c = G_c / eta (c < n), a_n = -sum_c G_c g_hat_c / eta.
+// dL/dphi of modes [k0, k1) (capped at the kept planes) from the quantity slices'
+// partial plane sets: the sets 1 .. slices-1 are added to set 0 in slice order, so
+// the result does not depend on the order in which the slices' CTAs ran.
+__global__ void k_dphi_slices(float* __restrict__ dphi, int slices, int64_t slice, int64_t N,
+                              int k0, int k1, const DevState* __restrict__ state) {
+  const int ke = min(k1, state->planes);
+  const int64_t total = (int64_t)(ke - k0) * N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t idx = (int64_t)k0 * N + e;
+    float v = dphi[idx];
+    for (int z = 1; z < slices; ++z) v += dphi[z * slice + idx];
+    dphi[idx] = v;
+  }
+}
+
 __global__ void k_adjoint(const float* __restrict__ gout, const float* __restrict__ out,
                           const float* __restrict__ eta, int64_t N, int n, float* __restrict__ adj) {
   for (int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pix < N;
@@ -428,8 +444,9 @@ cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spat
     count_launches(1);
   }
   const int chunks = bwd_chunks(Sc, n);
+  const int slices = bwd_dphi_slices(Sc, n);
   cudaError_t e;
-  if (chunks > 1 && first) {
+  if (chunks > 1 && slices == 1 && first) {
     e = cudaMemsetAsync(dphi, 0, sizeof(float) * (size_t)K * N, st);
     if (e != cudaSuccess) return e;
   }
@@ -465,12 +482,20 @@ cudaError_t launch_bwd_conv(const float* f, int H, int W, int n, int K, int spat
   a.k_end = k_end;
   a.accumulate = first ? 0 : 1;
   a.dphi = dphi;
-  a.atomic_dphi = chunks > 1 ? 1 : 0;
+  // two slices: atomic adds onto zero (commutative, so still one result); more:
+  // a plane set per slice, summed in slice order below
+  a.atomic_dphi = (chunks > 1 && slices == 1) ? 1 : 0;
+  a.dphi_slice = slices > 1 ? (int64_t)K * N : 0;
   a.df = grad_f;
   a.sig_part = spart;
-  if (Sc <= 8) return bwd_dispatch_a(Sc, a, st);
-  if (Sc <= 16) return bwd_dispatch_b(Sc, a, st);
-  return bwd_dispatch_c(Sc, a, st);
+  e = Sc <= 8 ? bwd_dispatch_a(Sc, a, st) : (Sc <= 16 ? bwd_dispatch_b(Sc, a, st) : bwd_dispatch_c(Sc, a, st));
+  if (e != cudaSuccess || slices == 1) return e;
+  int64_t g = ((int64_t)(k_end - k_begin) * N + 255) / 256;
+  if (g > 152 * 8) g = 152 * 8;
+  if (g < 1) g = 1;
+  k_dphi_slices<<<(int)g, 256, 0, st>>>(dphi, slices, (int64_t)K * N, N, k_begin, k_end, state);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_bwd_features(const float* f, const float* guide, int H, int W, int n, int rho,

@@ -21,6 +21,11 @@ int bwd_chunks(int Sc, int n) {
   return (n + 1 + nq - 1) / nq;
 }
 
+int bwd_dphi_slices(int Sc, int n) {
+  const int c = bwd_chunks(Sc, n);
+  return c > 2 ? c : 1;
+}
+
 int64_t bwd_ctas(int Sc, int H, int W, int n) {
   const int tw = Sc <= 16 ? 64 : (Sc <= 24 ? 48 : 32);
   return (int64_t)((W + tw - 1) / tw) * ((H + 31) / 32) * bwd_chunks(Sc, n);

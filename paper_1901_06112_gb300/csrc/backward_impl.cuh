@@ -50,12 +50,14 @@ struct BwdArgs {
   int accumulate;         // add into df and sig_part (a later chunk of modes) instead of writing
   int box;
   float* dphi;            // r planes of N
-  int atomic_dphi;        // quantities split over several CTAs: accumulate dphi atomically
+  int atomic_dphi;        // quantities split over two CTAs: accumulate dphi atomically
   float* df;              // N x n, direct image term
   float* sig_part;        // one sigma_s partial per CTA
   // (g(t), g(t)) and (g'(t), g'(t)) for t = 0..S_compiled, zero beyond the true radius
   float2 tg[kMaxTapRadius + 1];
   float2 td[kMaxTapRadius + 1];
+  int64_t dphi_slice;     // > 0: the CTAs of quantity slice z write their own plane set at
+                          // dphi + z dphi_slice (summed in a fixed order afterwards)
 };
 
 constexpr int kBwdThreads = 256;    // 8 warps; the taps live in the launch parameters (constant bank)
@@ -129,7 +131,7 @@ __device__ __forceinline__ void sym_fir(const float2* x, const float2* tg, const
   }
 }
 
-template <int S>
+template <int S, bool SLICES>
 __global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_constant__ BwdArgs a) {
   using C = BwdCfg<S>;
   constexpr int TH = C::TH, RV = C::RV, RH = C::RH, NQ = C::NQ, NP = C::NP;
@@ -300,6 +302,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) k_conv_bwd(const __grid_consta
     }
     if (yin) {
       float* dst = a.dphi + (int64_t)k * a.N + (int64_t)y * a.W;
+      if (SLICES) dst += blockIdx.z * a.dphi_slice;
 #pragma unroll
       for (int j = 0; j < RH; ++j) {
         const int x = tx0 + hx0 + j;
@@ -347,15 +350,21 @@ dim3 bwd_grid(int H, int W, int n) {
   return dim3((W + C::TW - 1) / C::TW, (H + C::TH - 1) / C::TH, (n + 1 + C::NQ - 1) / C::NQ);
 }
 
-template <int S>
-cudaError_t bwd_launch(const BwdArgs& a, cudaStream_t st) {
+template <int S, bool SLICES>
+cudaError_t bwd_launch_v(const BwdArgs& a, cudaStream_t st) {
   using C = BwdCfg<S>;
-  cudaError_t e = cudaFuncSetAttribute(k_conv_bwd<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)C::smem);
+  cudaError_t e = cudaFuncSetAttribute(k_conv_bwd<S, SLICES>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem);
   if (e != cudaSuccess) return e;
-  k_conv_bwd<S><<<bwd_grid<S>(a.H, a.W, a.n), kBwdThreads, C::smem, st>>>(a);
+  k_conv_bwd<S, SLICES><<<bwd_grid<S>(a.H, a.W, a.n), kBwdThreads, C::smem, st>>>(a);
   count_launches(1);
   return cudaGetLastError();
+}
+
+// the plane-set variant only where quantity slices write their own dL/dphi sets
+template <int S>
+cudaError_t bwd_launch(const BwdArgs& a, cudaStream_t st) {
+  return a.dphi_slice > 0 ? bwd_launch_v<S, true>(a, st) : bwd_launch_v<S, false>(a, st);
 }
 
 cudaError_t bwd_dispatch_a(int Sc, const BwdArgs& a, cudaStream_t st);   // 1..8

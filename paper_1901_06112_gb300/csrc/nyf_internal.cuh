@@ -48,6 +48,7 @@ struct WsShape {
   bool bwd;         // regions of the backward pass (saved convolutions, adjoints, partials)
   bool iir;         // recursive-Gaussian planes (omega_v * (phi_k f_c), K (n + 1) planes)
   bool recompute;   // backward recomputes C_kq: room for kRecomputeModes modes' planes only
+  int dphi_slices;  // backward: dL/dphi as this many partial plane sets (1: one set)
 };
 
 WsLayout ws_layout(const WsShape& s);
@@ -151,6 +152,10 @@ cudaError_t launch_conv_combine(const float* f, int H, int W, int n, const void*
                                 float* out, float* eta_out, float* zeta_ws, float* cout,
                                 cudaStream_t st);
 int conv_compiled_radius(int S);
+// Partial dL/dphi plane sets of the adjoint convolution for compiled radius Sc and
+// n channels: one per quantity slice when more than two CTAs share a tile (summed
+// in a fixed order afterwards), else 1 (direct writes, or two commutative adds).
+int bwd_dphi_slices(int Sc, int n);
 bool iir_supported(int H, int W, int n);
 cudaError_t launch_iir_combine(const float* f, int H, int W, int n, const float* phi, int K,
                                float sigma_s, DevState* state, float* out, float* eta_out,
