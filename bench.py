@@ -519,8 +519,10 @@ def config_line(nyf, lib, w, golden, precision, fwdbwd, steps, flush, stream):
     return line
 
 
-def batched_extra(nyf, steps, warmup, flush, stream, precision="bf16"):
-    """The 64-image workload (K = 16): forward + backward by CUDA-graph replay."""
+def batched_extra(nyf, steps, warmup, flush, stream, precision="bf16", tiles=None):
+    """The 64-image workload (K = 16): forward + backward by CUDA-graph replay.  tiles:
+    None (the library's choice per radius) or "tuned" (the autotuner's variant per
+    radius and image-size class, tuned before the timed region)."""
     import torch
     from paper_1901_06112_gb300 import synth
     batch = synth.batched_blf()
@@ -528,6 +530,8 @@ def batched_extra(nyf, steps, warmup, flush, stream, precision="bf16"):
     P = nyf.Params(K=16, kmeans_iters=10, precision=precision)
     bt = nyf.Batched(shapes, [w.sigma_s for w in batch], [w.sigma_r for w in batch], P)
     f = bt.pack([w.f for w in batch])
+    if tiles == "tuned":                           # before the timed region
+        bt.tune_tiles(f)
     G = torch.randn(f.shape, generator=torch.Generator().manual_seed(0)).cuda()
     bt.capture(f, G)
     for _ in range(warmup):
@@ -554,6 +558,9 @@ def batched_extra(nyf, steps, warmup, flush, stream, precision="bf16"):
             tot[k] = tuple(a + b for a, b in zip(tot.get(k, (0.0,) * 4), v))
     roof = step_roofline(tot, {}, t)
     line = {"workload": f"batched_blf_64_images_128-1024_K16_{precision}", "images": len(batch),
+            "tiles": ("tuned in the batch (Batched.tune_tiles): " + ", ".join(
+                f"{t} {bt.tiles.count(t)}" for t in sorted(set(bt.tiles))))
+            if tiles == "tuned" else "library default",
             "megapixels": mpix, "ms_per_step": t, "value": mpix / (t / 1e3),
             "unit": "megapixels/s", "mode": "fwd+bwd, one CUDA-graph replay per step",
             "roofline_step": roof}
@@ -843,9 +850,11 @@ def main():
                                   stream, lib)
             extras[other] = {"fwdbwd_value" if fwdbwd else "value": mp / (o_ms / 1e3),
                              "fwd_value": mp / (f_ms / 1e3), "unit": "megapixels/s"}
-        for prec, key in (("bf16", "batched"), ("fp32", "batched_fp32")):
+        for prec, key, tiles in (("bf16", "batched", None), ("fp32", "batched_fp32", None),
+                                 ("bf16", "batched_tuned", "tuned")):
             try:
-                extras[key] = batched_extra(nyf, max(3, args.steps // 4), 2, flush, stream, prec)
+                extras[key] = batched_extra(nyf, max(3, args.steps // 4), 3, flush, stream, prec,
+                                            tiles)
             except Exception as ex:               # the side measurement must not hide the main one
                 extras[key] = {"error": str(ex)[:300]}
         if not iir:

@@ -353,6 +353,14 @@ class Batched:
         params = params.for_backward() if backward else params
         self.params = params
         self.items = (L.NyfBatchItem * self.B)()
+        # the library's window radius: ceil(3 sigma_s) of the float32 sigma_s
+        self.radii = [params.S if params.S > 0 else math.ceil(3.0 * C.c_float(float(s)).value)
+                      for s in sigmas_s]
+        if tiles == "tuned":                     # the autotuner's variant per radius and size
+            from . import tune
+            tiles = tune.tune_images([(int(H), int(W)) for H, W in shapes], self.radii, params.K,
+                                     params.precision)
+        self.tiles = list(tiles) if tiles else None
         off = 0
         self.offsets = []
         for b, (H, W) in enumerate(shapes):
@@ -380,6 +388,57 @@ class Batched:
         for (H, W), o in zip(self.shapes, self.offsets):
             out.append(flat[o:o + H * W * self.n].view(H, W, self.n))
         return out
+
+    def set_tiles(self, tiles):
+        """Convolution variant per image ("wide", "narrow", "tensor" or "auto")."""
+        for b, t in enumerate(tiles):
+            self.items[b].conv_tile = self.TILES[t]
+        self.tiles = list(tiles)
+
+    def tune_tiles(self, f, landmarks=None, reps=3, gain=0.01):
+        """Tunes the convolution variants in the batch itself: starting from the
+        library's defaults, each group of images with the same radius and size class
+        tries the other variants, and a change is kept when the whole batch's forward
+        gets faster by more than `gain` (the images share the GPU, so an image's best
+        variant alone is not always the batch's).  Returns the tiles it keeps."""
+        from . import tune
+        n3 = self.n <= 3
+        cur = ["tensor" if self.params.precision == "bf16" and S <= 16 and n3 else "wide"
+               for S in self.radii]
+        groups = {}
+        for b, ((H, W), S) in enumerate(zip(self.shapes, self.radii)):
+            groups.setdefault((S, tune.size_class(H, W)), []).append(b)
+        out = torch.empty_like(f)
+
+        def run(tiles):
+            self.set_tiles(tiles)
+            self.forward(f, out, landmarks)
+            torch.cuda.synchronize()
+            best = math.inf
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(torch.cuda.current_stream())
+                self.forward(f, out, landmarks)
+                e1.record(torch.cuda.current_stream())
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            return best
+
+        best_t = run(cur)
+        for (S, _), idx in sorted(groups.items()):
+            cands = [c for c in tune.candidates(S, self.params.precision)
+                     if not (c == "tensor" and not n3)]
+            for c in cands:
+                if c == cur[idx[0]]:
+                    continue
+                trial = list(cur)
+                for b in idx:
+                    trial[b] = c
+                t = run(trial)
+                if t < best_t * (1.0 - gain):
+                    best_t, cur = t, trial
+        self.set_tiles(cur)
+        return cur
 
     def forward(self, f, out=None, landmarks=None):
         """Forward of every image; landmarks: None (k-means per image) or a

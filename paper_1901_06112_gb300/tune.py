@@ -1,11 +1,13 @@
-"""Autotuner of the convolution variant per window radius.
+"""Autotuner of the convolution variant per window radius and image size.
 
-For each radius S (and precision) it times the candidate kernels of the
-convolution + combine stage -- FP32 FIR with 32 x 96 or 32 x 64 tiles, and
-the BF16 tensor-core kernel when the precision allows it -- on a synthetic
-512 x 512 colour image with K landmarks, and keeps the fastest.  Results are
-cached in a JSON file (NYF_TUNE_CACHE, default ~/.cache/nyf_tune.json) keyed
-by device name, radius, K and precision.
+For each radius S, image-size class and precision it times the candidate
+kernels of the convolution + combine stage -- FP32 FIR with 32 x 96 or
+32 x 64 tiles, and the BF16 tensor-core kernel when the precision allows it --
+on a synthetic square colour image of the class's side (256, 512 or 1024
+pixels: the tile shapes trade halo work against the last wave's idle SMs, which
+depends on the image size) with K landmarks, and keeps the fastest.  Results
+are cached in a JSON file (NYF_TUNE_CACHE, default ~/.cache/nyf_tune.json)
+keyed by device name, radius, size class, K and precision.
 """
 from __future__ import annotations
 
@@ -68,12 +70,24 @@ def time_variant(S: int, K: int, precision: str, tile: str, size=512, reps=3) ->
     return best
 
 
-def best_variant(S: int, K: int, precision: str, refresh=False) -> str:
-    key = f"{torch.cuda.get_device_name()}|S={S}|K={K}|{precision}"
+SIZE_CLASSES = (256, 512, 1024)
+
+
+def size_class(H: int, W: int) -> int:
+    """The tuning side for an H x W image: the class nearest to sqrt(H W) on a log scale."""
+    side = math.sqrt(max(1, H * W))
+    return min(SIZE_CLASSES, key=lambda c: abs(math.log(side / c)))
+
+
+def best_variant(S: int, K: int, precision: str, size: int = 512, refresh=False) -> str:
+    cands = candidates(S, precision)
+    if len(cands) == 1:
+        return cands[0]
+    key = f"{torch.cuda.get_device_name()}|S={S}|size={size}|K={K}|{precision}"
     cache = _load()
     if not refresh and key in cache:
         return cache[key]["best"]
-    times = {t: time_variant(S, K, precision, t) for t in candidates(S, precision)}
+    times = {t: time_variant(S, K, precision, t, size=size) for t in cands}
     best = min(times, key=times.get)
     cache[key] = {"best": best, "ms": times}
     _save(cache)
@@ -81,5 +95,11 @@ def best_variant(S: int, K: int, precision: str, refresh=False) -> str:
 
 
 def tune_batch(radii, K: int, precision: str, refresh=False):
-    """Best variant for every distinct radius of a batch."""
-    return {S: best_variant(S, K, precision, refresh) for S in sorted(set(radii))}
+    """Best variant for every distinct radius of a batch (512-pixel class)."""
+    return {S: best_variant(S, K, precision, 512, refresh) for S in sorted(set(radii))}
+
+
+def tune_images(shapes, radii, K: int, precision: str, refresh=False):
+    """Best variant for every image of a batch: by its radius and size class."""
+    return [best_variant(S, K, precision, size_class(H, W), refresh)
+            for (H, W), S in zip(shapes, radii)]

@@ -261,6 +261,24 @@ def test_autotuner_picks_a_valid_variant(nyf, tmp_path, monkeypatch):
     assert best[21] == "wide"
     assert (tmp_path / "tune.json").exists()
     print(f"[parity] autotuned variants: {best}")
+    # per image: by radius and size class; a tuned batch equals per-image calls with those tiles
+    shapes, ss = [(200, 180), (700, 650), (120, 260)], [2.0, 5.0, 7.0]
+    assert [tune.size_class(H, W) for H, W in shapes] == [256, 512, 256]
+    P = nyf.Params(K=6, kmeans_iters=2, precision="bf16")
+    bt = nyf.Batched(shapes, ss, [30.0, 40.0, 50.0], P, tiles="tuned")
+    assert bt.tiles[2] == "wide" and all(t in ("wide", "narrow", "tensor") for t in bt.tiles)
+    imgs = [synth.voronoi_colour(H, W, 12, 8.0, 700 + b) for b, (H, W) in enumerate(shapes)]
+    out = bt.unpack(bt.forward(bt.pack(imgs)))
+    for b, (H, W) in enumerate(shapes):
+        Pb = nyf.Params(sigma_s=ss[b], sigma_r=[30.0, 40.0, 50.0][b], K=6, kmeans_iters=2,
+                        precision="bf16", conv_tile=bt.tiles[b], save_for_backward=True)
+        ob = nyf.blf(torch.from_numpy(imgs[b]).cuda(), Pb)
+        assert torch.equal(out[b], ob), b
+    # tuning in the batch itself keeps valid variants (the default where nothing is faster)
+    kept = bt.tune_tiles(bt.pack(imgs), reps=2)
+    assert kept == bt.tiles and kept[2] == "wide"
+    assert all(t in ("wide", "narrow", "tensor") for t in kept)
+    print(f"[parity] variants tuned in the batch: {kept}")
 
 
 def test_deep_guide_batch_equals_per_image_calls(nyf):
