@@ -140,3 +140,31 @@ def test_pca_nlm_host_checks(lib):
                                   None) == 3
     assert lib.nyf_patch_pca(bad, 64, 64, 3, 3, 26, bad, bad, bad, bad, 16, None) == 3
     assert lib.nyf_patch_pca(bad, 64, 64, 3, 3, 148, bad, bad, bad, bad, 16, None) == 1
+
+
+def test_backward_workspace_holds_a_dphi_set_per_quantity_slice(lib):
+    # n = 31 channels at S = 12: the 32 quantities form 8 slices of 4 per tile, so the
+    # backward keeps 8 partial dL/dphi plane sets (summed in slice order) besides the
+    # K (n + 1) convolved planes; n = 3 needs neither
+    K, H, W = 8, 64, 64
+    N = H * W
+    p = _lib.NyfParams(4.0, 0.15, K, 10, 0, 1e-7, 0, 0, 0, 0, 1.0, 0)
+    fwd = lib.nyf_workspace_size(H, W, 31, 31, C.byref(p))
+    p.save_for_backward = 1
+    bwd = lib.nyf_workspace_size(H, W, 31, 31, C.byref(p))
+    assert bwd - fwd >= 4 * N * (K * 32 + 8 * K)
+    p.save_for_backward = 0
+    fwd3 = lib.nyf_workspace_size(H, W, 3, 3, C.byref(p))
+    p.save_for_backward = 1
+    bwd3 = lib.nyf_workspace_size(H, W, 3, 3, C.byref(p))
+    assert bwd3 - fwd3 < 4 * N * (K * 4 + 2 * K) + 4 * N * 8 + (1 << 20)
+
+
+def test_autotuner_size_classes():
+    from paper_1901_06112_gb300 import tune
+    assert [tune.size_class(H, W) for H, W in [(128, 128), (300, 400), (512, 512), (600, 650),
+                                               (1024, 1024), (4000, 3000)]] == \
+        [256, 256, 512, 512, 1024, 1024]
+    assert tune.candidates(15, "fp32") == ["wide", "narrow"]
+    assert tune.candidates(15, "bf16") == ["wide", "narrow", "tensor"]
+    assert tune.candidates(21, "bf16") == ["wide"]
