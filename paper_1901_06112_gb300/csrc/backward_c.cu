@@ -27,7 +27,7 @@ int bwd_dphi_slices(int Sc, int n) {
 }
 
 int64_t bwd_ctas(int Sc, int H, int W, int n) {
-  const int tw = Sc <= 16 ? 64 : (Sc <= 24 ? 48 : 32);
+  const int tw = Sc <= 24 ? 64 : 32;
   return (int64_t)((W + tw - 1) / tw) * ((H + 31) / 32) * bwd_chunks(Sc, n);
 }
 }  // namespace nyf

@@ -65,7 +65,7 @@ constexpr int kBwdThreads = 256;    // 8 warps; the taps live in the launch para
 template <int S>
 struct BwdCfg {
   static constexpr int TH = 32;                                 // = lanes: one row per lane
-  static constexpr int TW = S <= 16 ? 64 : (S <= 24 ? 48 : 32);
+  static constexpr int TW = S <= 16 ? 64 : (S <= 24 ? 64 : 32);
   static constexpr int RV = 8;                                  // rows per vertical task
   static constexpr int NQ = S <= 16 ? 4 : 2;                    // quantities per CTA
   static constexpr int NP = NQ / 2;                             // quantity pairs
